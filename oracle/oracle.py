@@ -1,0 +1,247 @@
+"""ctypes loader for the CPU FP64 oracle (rrq_oracle.c).
+
+TEST INFRASTRUCTURE: only the tests, the smoke check and the CPU-baseline leg of
+the benchmark import this module.  The product path (the CUDA library and its
+binding) never does.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "librrq_oracle.so")
+_SRC = os.path.join(_HERE, "rrq_oracle.c")
+PMAX = 12
+KERNELS = ("S", "D", "SP", "DP")
+MASK = {"S": 1, "D": 2, "SP": 4, "DP": 8}
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Opts(C.Structure):
+    _fields_ = [("ptilde", C.c_int), ("rho0", C.c_double), ("newton_max", C.c_int),
+                ("eta", C.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _lib.orc_surface_create.restype = C.c_void_p
+            _lib.orc_surface_destroy.argtypes = [C.c_void_p]
+            _lib.orc_T.restype = C.c_double
+            for name in ("orc_near", "orc_rows", "orc_patch_internals", "orc_edge_root",
+                         "orc_pair_B", "orc_patch_bounds"):
+                getattr(_lib, name).restype = C.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class OracleSurface:
+    """Holds a surface for the oracle.  Arrays are kept alive by this object."""
+
+    def __init__(self, disc, ptilde: int = 0, rho0: float = 0.0, newton_max: int = 0,
+                 eta: float = 0.0):
+        L = lib()
+        self.d = disc
+        self.order = np.ascontiguousarray(disc.order, dtype=np.int32)
+        self.node_off = np.ascontiguousarray(disc.node_off, dtype=np.int64)
+        self.xyz = np.ascontiguousarray(disc.xyz, dtype=np.float64)
+        self.nrm = np.ascontiguousarray(disc.nrm, dtype=np.float64)
+        self.wts = np.ascontiguousarray(disc.wts, dtype=np.float64)
+        self._uv = {p: np.ascontiguousarray(uv, dtype=np.float64) for p, uv in disc.ref_uv.items()}
+        arr = (C.c_void_p * (PMAX + 1))()
+        for p, uv in self._uv.items():
+            arr[p] = uv.ctypes.data
+        self._arr = arr
+        self.opts = _Opts(ptilde, rho0, newton_max, eta)
+        self.h = L.orc_surface_create(C.c_int(disc.npatch), _p(self.order), _p(self.node_off),
+                                      _p(self.xyz), _p(self.nrm), _p(self.wts), arr,
+                                      C.byref(self.opts))
+        if not self.h:
+            raise RuntimeError("oracle surface creation failed")
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().orc_surface_destroy(C.c_void_p(self.h))
+                self.h = None
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- near lists
+    def near(self, targets, tsel=None):
+        """Near patches per selected target: (rowptr (nsel+1), patches)."""
+        nt = targets.n
+        tsel = np.arange(nt, dtype=np.int64) if tsel is None else np.ascontiguousarray(tsel, np.int64)
+        txyz = np.ascontiguousarray(targets.xyz, np.float64)
+        tself = np.ascontiguousarray(targets.self_node, np.int64)
+        counts = np.zeros(len(tsel), np.int64)
+        L = lib()
+        L.orc_near(C.c_void_p(self.h), C.c_int64(len(tsel)), _p(tsel), _p(txyz), _p(tself),
+                   _p(counts), None, None)
+        offs = np.zeros(len(tsel) + 1, np.int64)
+        np.cumsum(counts, out=offs[1:])
+        pairs = np.zeros(max(1, int(offs[-1])), np.int32)
+        L.orc_near(C.c_void_p(self.h), C.c_int64(len(tsel)), _p(tsel), _p(txyz), _p(tself),
+                   _p(counts), _p(offs), _p(pairs))
+        return offs, pairs[: offs[-1]]
+
+    # ------------------------------------------------------------------- rows
+    def rows(self, targets, pair_t, pair_P, kernels=KERNELS):
+        """Correction rows for explicit pairs: dict kernel -> (npair, n_p) array (uniform p)."""
+        pair_t = np.ascontiguousarray(pair_t, np.int64)
+        pair_P = np.ascontiguousarray(pair_P, np.int32)
+        npair = len(pair_t)
+        npn = (self.node_off[1:] - self.node_off[:-1])[pair_P] if npair else np.zeros(0, np.int64)
+        val_off = np.zeros(npair, np.int64)
+        if npair:
+            val_off[1:] = np.cumsum(npn)[:-1]
+        tot = int(npn.sum()) if npair else 0
+        mask = 0
+        for k in kernels:
+            mask |= MASK[k]
+        vals = {k: np.zeros(max(tot, 1)) for k in KERNELS}
+        flags = np.zeros(max(npair, 1), np.int32)
+        L = lib()
+        r = L.orc_rows(C.c_void_p(self.h), C.c_int64(npair), _p(pair_t), _p(pair_P),
+                       _p(np.ascontiguousarray(targets.xyz, np.float64)),
+                       _p(np.ascontiguousarray(targets.nrm, np.float64)),
+                       _p(np.ascontiguousarray(targets.self_node, np.int64)), C.c_uint(mask),
+                       _p(val_off), _p(vals["S"]), _p(vals["D"]), _p(vals["SP"]), _p(vals["DP"]),
+                       _p(flags))
+        if r != 0:
+            raise RuntimeError("oracle rows failed (singular fit)")
+        return {k: vals[k][:tot] for k in kernels}, val_off, flags[:npair]
+
+    def csr_rows(self, targets, tsel=None, kernels=KERNELS):
+        """CSR restricted to the selected target rows: (rowptr, col, {kernel: val}, flags)."""
+        offs, pairs = self.near(targets, tsel)
+        tsel = np.arange(targets.n) if tsel is None else np.asarray(tsel)
+        pair_t = np.repeat(tsel, np.diff(offs))
+        vals, val_off, flags = self.rows(targets, pair_t, pairs, kernels)
+        npn = self.node_off[1:] - self.node_off[:-1]
+        rowlen = np.zeros(len(tsel), np.int64)
+        np.add.at(rowlen, np.repeat(np.arange(len(tsel)), np.diff(offs)), npn[pairs])
+        rowptr = np.zeros(len(tsel) + 1, np.int64)
+        np.cumsum(rowlen, out=rowptr[1:])
+        col = np.concatenate([np.arange(self.node_off[P], self.node_off[P + 1]) for P in pairs]).astype(np.int32) \
+            if len(pairs) else np.zeros(0, np.int32)
+        return rowptr, col, vals, flags
+
+    # -------------------------------------------------------------- internals
+    def patch_internals(self, P: int):
+        p = int(self.order[P])
+        npn = p * (p + 1) // 2
+        pt = self.opts.ptilde if self.opts.ptilde > 0 else 2 * p
+        out = dict(frame=np.zeros(13), vert=np.zeros(9), y=np.zeros(npn * 3), ea=np.zeros(9 * p),
+                   ey=np.zeros(9 * pt), et=np.zeros(9 * pt), XD=np.zeros(4 * npn * npn),
+                   XSp=np.zeros(4 * npn * npn), XS1=np.zeros(npn * npn), XS2=np.zeros(4 * npn * npn))
+        r = lib().orc_patch_internals(C.c_void_p(self.h), C.c_int(P), *[_p(out[k]) for k in
+                                      ("frame", "vert", "y", "ea", "ey", "et", "XD", "XSp", "XS1", "XS2")])
+        out["status"] = r
+        out["c"] = out["frame"][:3]
+        out["R"] = out["frame"][3:12].reshape(3, 3)
+        out["s"] = out["frame"][12]
+        out["vert"] = out["vert"].reshape(3, 3)
+        out["y"] = out["y"].reshape(npn, 3)
+        out["ea"] = out["ea"].reshape(3, p, 3)
+        out["ey"] = out["ey"].reshape(3, pt, 3)
+        out["et"] = out["et"].reshape(3, pt, 3)
+        for k in ("XD", "XSp", "XS2"):
+            out[k] = out[k].reshape(4 * npn, npn)
+        out["XS1"] = out["XS1"].reshape(npn, npn)
+        return out
+
+    def pair_B(self, P: int, xt, nt, self_i: int = -1):
+        p = int(self.order[P])
+        npn = p * (p + 1) // 2
+        B, dB, Psi, Om, dOm = np.zeros(4 * npn), np.zeros(4 * npn), np.zeros(npn), np.zeros(4), np.zeros(4)
+        fl = lib().orc_pair_B(C.c_void_p(self.h), C.c_int(P), _p(np.ascontiguousarray(xt, np.float64)),
+                              _p(np.ascontiguousarray(nt, np.float64)), C.c_int(self_i),
+                              _p(B), _p(Psi), _p(dB), _p(Om), _p(dOm))
+        return dict(B=B.reshape(npn, 4), Psi=Psi, dB=dB.reshape(npn, 4), Om=Om, dOm=dOm, flags=fl)
+
+    def edge_root(self, P: int, e: int, yt):
+        t0 = np.zeros(2)
+        c = lib().orc_edge_root(C.c_void_p(self.h), C.c_int(P), C.c_int(e),
+                                _p(np.ascontiguousarray(yt, np.float64)), _p(t0))
+        return complex(t0[0], t0[1]), bool(c)
+
+
+# ------------------------------------------------------------------ free functions
+
+def solid_S(L: int, y) -> np.ndarray:
+    out = np.zeros(2 * (L + 1) ** 2)
+    lib().orc_solid_S(C.c_int(L), _p(np.ascontiguousarray(y, np.float64)), _p(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def solid_R(L: int, xyz) -> np.ndarray:
+    out = np.zeros(2 * (L + 1) ** 2)
+    lib().orc_solid_R(C.c_int(L), _p(np.ascontiguousarray(xyz, np.float64)), _p(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def grad_hess_S(L: int, y, l: int, m: int):
+    g, H = np.zeros(6), np.zeros(18)
+    lib().orc_grad_hess_S(C.c_int(L), _p(np.ascontiguousarray(y, np.float64)), C.c_int(l), C.c_int(m),
+                          _p(g), _p(H))
+    return g[0::2] + 1j * g[1::2], (H[0::2] + 1j * H[1::2]).reshape(3, 3)
+
+
+def hidx(n: int, q: int) -> int:
+    return n * n + n + q
+
+
+def T(j, k, l, m) -> float:
+    return lib().orc_T(C.c_int(j), C.c_int(k), C.c_int(l), C.c_int(m))
+
+
+def gauss_legendre(n: int):
+    x, w = np.zeros(n), np.zeros(n)
+    lib().orc_gauss_legendre(C.c_int(n), _p(x), _p(w))
+    return x, w
+
+
+def ssq_moments(n: int, a: float, b: float):
+    J, K = np.zeros(n), np.zeros(n)
+    lib().orc_ssq_moments(C.c_int(n), C.c_double(a), C.c_double(b), _p(J), _p(K))
+    return J, K
+
+
+def bernstein_rho(z: complex) -> float:
+    r = C.c_double()
+    lib().orc_bernstein_rho(C.c_double(z.real), C.c_double(z.imag), C.byref(r))
+    return r.value
+
+
+def lu_solve(A, B):
+    A = np.ascontiguousarray(A, np.float64)
+    B = np.ascontiguousarray(B, np.float64).copy()
+    nrhs = 1 if B.ndim == 1 else B.shape[1]
+    r = lib().orc_lu_solve(C.c_int(A.shape[0]), _p(A), C.c_int(nrhs), _p(B))
+    if r:
+        raise np.linalg.LinAlgError("singular")
+    return B

@@ -1,0 +1,1345 @@
+/*
+ * rrq_oracle.c -- CPU FP64 oracle for the recursive reduction quadrature (RRQ)
+ * near-field correction rows of the Laplace S, D, S', D' operators
+ * (Jiang & Zhu, "Recursive reduction quadrature for the evaluation of Laplace
+ * layer potentials in three dimensions", arXiv 2411.08342).
+ *
+ * TEST INFRASTRUCTURE.  This file is the slow, plain reference that the CUDA
+ * library is checked against.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load it.  It shares no code, header or table
+ * generator with the CUDA library.
+ *
+ * Every step follows the paper's algorithm in its order and notation:
+ *   - regular solid harmonics R_l^m from the Legendre recurrence (Sec. 2.3,
+ *     eqs. associatelegendrerecurrence, ylmdef, rlmdef), S^{(l,m)}(x,y,z) =
+ *     R_l^m(y,z,x) and H^{(l,m)} = sqrt2 Im S^{(l,m)} (eqs. slmdef, hlmslmconnection);
+ *   - the translation formula with T_{jk,lm} (eqs. l2ltranslation, tjklmdef),
+ *     used also to differentiate S (its j=1 and j=2 terms);
+ *   - the quaternion harmonic fit (eq. dlpdensitylinearsystem2), the scalar
+ *     SLP fit (eq. slpdensitylinearsystem) and the S' fit
+ *     (eq. sprimedensitylinearsystem), solved by LU with partial pivoting;
+ *   - target-centred 1-forms (Thms. dlp1form, cslp1form), line integrals
+ *     (eqs. lineintegrals, solidangle), singularity-swap quadrature (Sec. 2.4,
+ *     Sec. 3.4: root t0, moments, c = U F), the D' line integrals
+ *     (eq. dprimelineintegrals), and Step 8 (eq. wlmdef) with the matrix-build
+ *     remark of Sec. 4.
+ *
+ * Readings where the paper is silent or inconsistent (each one is applied
+ * identically by the CUDA path, which implements it independently):
+ *   - S' sign: S'[sigma] = -int nu'.grad_r G sigma; with the fit of (0, sigma nu)
+ *     the row is -[(0,nu') sum B^{lm} w^{lm}]_0 (the printed eq. sprime1formrep
+ *     has the opposite overall sign).
+ *   - the S^{(l,m)}(r') omega_0 term of Thm. cslp1form carries 1/(4 pi).
+ *   - frame: origin = vertex mean, e_z = unit((V1-V0)x(V2-V0)), e_x along the
+ *     longest edge (first of E0,E1,E2 on ties), scale 1/longest edge.
+ *   - u: +e_z for a target that is a node of the patch; otherwise whichever of
+ *     +e_z, -e_z maximises the minimum of u.(r'-r)/|r'-r| over the nodes and edge
+ *     samples.
+ *   - Omega_0 sign: Thm. dlp1form needs (1/4pi) d omega_0 = -grad_r G . nu da, but the
+ *     printed omega_0 (eq. omega0def) integrates to +4 pi int grad_r G . nu da (checked
+ *     on a disc by hand), so Omega_0 = - (line integral of the printed omega_0); its
+ *     nu' derivative (eq. dprimelineintegrals) is negated the same way.
+ *   - Omega_0 and its nu' derivative: composite Gauss-Legendre on panels graded
+ *     geometrically toward Re t0 (the "mild adaptive" integration of Sec. 3.4).
+ *   - the SSQ is used when the Bernstein radius of t0 is below rho0; otherwise
+ *     the modified weights are formed by a 2*ptilde point Gauss rule applied to
+ *     the Lagrange basis of the ptilde edge nodes.
+ *   - on-surface (self) pairs return the principal value for D and S'
+ *     (jump 1/2 applied at the coincident node), S and D' as computed.
+ *   - correction = RRQ row - smooth row (K(x_t, x_i) w_i, coincident node skipped).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define ORC_PMAX 12
+#define ORC_LMAX 16
+#define ORC_PTMAX 32
+#define ORC_NOM 16
+#define HIDX(n, q) ((n) * (n) + (n) + (q))
+#define NHFULL(L) (((L) + 1) * ((L) + 1))
+
+enum { ORC_S = 1, ORC_D = 2, ORC_SP = 4, ORC_DP = 8 };
+enum { FLAG_NEWTON = 1, FLAG_ONEDGE = 2, FLAG_UPOOR = 4, FLAG_SINGULAR = 8 };
+
+typedef struct {
+    int ptilde;      /* GL nodes per edge; <=0 -> 2p */
+    double rho0;     /* SSQ Bernstein-radius threshold; <=0 -> 10^(5/ptilde) */
+    int newton_max;  /* <=0 -> 30 */
+    double eta;      /* near factor; <=0 -> 1 */
+} orc_opts;
+
+/* ------------------------------------------------------------------------- */
+/* small numerics                                                             */
+/* ------------------------------------------------------------------------- */
+
+static double g_binom[2 * ORC_LMAX + 2][2 * ORC_LMAX + 2];
+static int g_binom_ready = 0;
+
+static void binom_init(void) {
+    if (g_binom_ready) return;
+    for (int n = 0; n < 2 * ORC_LMAX + 2; n++) {
+        for (int k = 0; k < 2 * ORC_LMAX + 2; k++) g_binom[n][k] = 0.0;
+        g_binom[n][0] = 1.0;
+        for (int k = 1; k <= n; k++) g_binom[n][k] = g_binom[n - 1][k - 1] + (k <= n - 1 ? g_binom[n - 1][k] : 0.0);
+    }
+    g_binom_ready = 1;
+}
+
+static double binom(int n, int k) {
+    if (n < 0 || k < 0 || k > n) return 0.0;
+    return g_binom[n][k];
+}
+
+static double factd(int n) {
+    double r = 1.0;
+    for (int i = 2; i <= n; i++) r *= i;
+    return r;
+}
+
+/* T_{jk,lm}, eq. (tjklmdef); zero when a binomial index is out of range. */
+static double Tcoef(int j, int k, int l, int m) {
+    return sqrt(binom(l + m, j + k) * binom(l - m, j - k));
+}
+
+/* C_{j,l} = int_0^1 t^{j-2}(1-t)^{l-j} dt (Thm. dlp1form) */
+static double Ccoef(int j, int l) { return factd(j - 2) * factd(l - j) / factd(l - 1); }
+/* D_{j,l} = int_0^1 t^{j-1}(1-t)^{l-j} dt (Thm. cslp1form) */
+static double Dcoef(int j, int l) { return factd(j - 1) * factd(l - j) / factd(l); }
+
+/* Gauss-Legendre nodes and weights on [-1,1] by Newton on P_n. */
+static void gauss_legendre(int n, double *x, double *w) {
+    for (int i = 0; i < n; i++) {
+        double t = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = t; p0 = 1.0; }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) {
+                /* recompute derivative at the converged point */
+                p0 = 1.0; p1 = t;
+                for (int k = 2; k <= n; k++) {
+                    double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                    p0 = p1; p1 = p2;
+                }
+                if (n == 1) { p1 = t; p0 = 1.0; }
+                dp = n * (t * p1 - p0) / (t * t - 1.0);
+                break;
+            }
+        }
+        x[n - 1 - i] = t;
+        w[n - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+/* In-place LU with partial pivoting of the n x n row-major matrix a; piv[n]. */
+static int lu_factor(int n, double *a, int *piv) {
+    for (int k = 0; k < n; k++) {
+        int pr = k;
+        double mx = fabs(a[k * n + k]);
+        for (int i = k + 1; i < n; i++)
+            if (fabs(a[i * n + k]) > mx) { mx = fabs(a[i * n + k]); pr = i; }
+        piv[k] = pr;
+        if (mx == 0.0) return -1;
+        if (pr != k)
+            for (int j = 0; j < n; j++) { double t = a[k * n + j]; a[k * n + j] = a[pr * n + j]; a[pr * n + j] = t; }
+        for (int i = k + 1; i < n; i++) {
+            double f = a[i * n + k] / a[k * n + k];
+            a[i * n + k] = f;
+            for (int j = k + 1; j < n; j++) a[i * n + j] -= f * a[k * n + j];
+        }
+    }
+    return 0;
+}
+
+/* Solve with the factors for nrhs right-hand sides stored as columns of b (n x nrhs). */
+static void lu_solve(int n, const double *lu, const int *piv, int nrhs, double *b) {
+    for (int k = 0; k < n; k++)
+        if (piv[k] != k)
+            for (int c = 0; c < nrhs; c++) { double t = b[k * nrhs + c]; b[k * nrhs + c] = b[piv[k] * nrhs + c]; b[piv[k] * nrhs + c] = t; }
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < i; k++) {
+            double f = lu[i * n + k];
+            if (f != 0.0)
+                for (int c = 0; c < nrhs; c++) b[i * nrhs + c] -= f * b[k * nrhs + c];
+        }
+    for (int i = n - 1; i >= 0; i--) {
+        for (int k = i + 1; k < n; k++) {
+            double f = lu[i * n + k];
+            if (f != 0.0)
+                for (int c = 0; c < nrhs; c++) b[i * nrhs + c] -= f * b[k * nrhs + c];
+        }
+        for (int c = 0; c < nrhs; c++) b[i * nrhs + c] /= lu[i * n + i];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Harmonic polynomials (Sec. 2.3)                                            */
+/* ------------------------------------------------------------------------- */
+
+/* R_l^m(X,Y,Z) for 0<=l<=L, -l<=m<=l, into R[HIDX(l,m)].  The recurrence of eq.
+ * (associatelegendrerecurrence) is applied to W_l^m = r^l P_l^m(Z/r) e^{i m phi},
+ * which removes every division by r; then R_l^m = sqrt((l-m)!/(l+m)!) W_l^m
+ * (eqs. ylmdef, rlmdef) and R_l^{-m} = (-1)^m conj(R_l^m). */
+static void solid_R(int L, double X, double Y, double Z, cplx *R) {
+    cplx W[ORC_LMAX + 1][ORC_LMAX + 1];
+    double r2 = X * X + Y * Y + Z * Z;
+    W[0][0] = 1.0;
+    for (int l = 0; l < L; l++) {
+        W[l + 1][l + 1] = -(2.0 * l + 1.0) * (X + I * Y) * W[l][l];
+        W[l + 1][l] = (2.0 * l + 1.0) * Z * W[l][l];
+        for (int m = 0; m <= l - 1; m++)
+            W[l + 1][m] = ((2.0 * l + 1.0) * Z * W[l][m] - (l + m) * r2 * W[l - 1][m]) / (l - m + 1.0);
+    }
+    for (int l = 0; l <= L; l++)
+        for (int m = 0; m <= l; m++) {
+            cplx v = sqrt(factd(l - m) / factd(l + m)) * W[l][m];
+            R[HIDX(l, m)] = v;
+            if (m > 0) R[HIDX(l, -m)] = ((m & 1) ? -1.0 : 1.0) * conj(v);
+        }
+}
+
+/* S^{(l,m)}(x,y,z) = R_l^m(y,z,x), eq. (slmdef). */
+static void solid_S(int L, const double y[3], cplx *S) { solid_R(L, y[1], y[2], y[0], S); }
+
+static cplx Sget(const cplx *S, int L, int n, int q) {
+    if (n < 0 || n > L || q < -n || q > n) return 0.0;
+    return S[HIDX(n, q)];
+}
+
+/* Constant gradients of S^{(1,k)} and Hessians of S^{(2,k)}: S^{(1,k)} is linear and
+ * S^{(2,k)} quadratic, so g_k[a] = S^{(1,k)}(e_a) and
+ * H_k[a][b] = S(e_a+e_b) - S(e_a) - S(e_b). */
+static cplx g1[3][3];      /* [k+1][a] */
+static cplx h2[5][3][3];   /* [k+2][a][b] */
+static int g_lowdeg_ready = 0;
+
+static void lowdeg_init(void) {
+    if (g_lowdeg_ready) return;
+    binom_init();
+    cplx S[NHFULL(2)], Sa[NHFULL(2)], Sb[NHFULL(2)];
+    for (int a = 0; a < 3; a++) {
+        double ea[3] = {0, 0, 0};
+        ea[a] = 1.0;
+        solid_S(1, ea, S);
+        for (int k = -1; k <= 1; k++) g1[k + 1][a] = S[HIDX(1, k)];
+    }
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            double eab[3] = {0, 0, 0}, ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
+            eab[a] += 1.0; eab[b] += 1.0; ea[a] = 1.0; eb[b] = 1.0;
+            solid_S(2, eab, S);
+            solid_S(2, ea, Sa);
+            solid_S(2, eb, Sb);
+            for (int k = -2; k <= 2; k++) h2[k + 2][a][b] = S[HIDX(2, k)] - Sa[HIDX(2, k)] - Sb[HIDX(2, k)];
+        }
+    g_lowdeg_ready = 1;
+}
+
+/* grad S^{(l,m)}(y) from the j=1 terms of the translation (eq. l2ltranslation):
+ * grad S^{(l,m)}(y) = sum_k grad S^{(1,k)} S^{(l-1,m-k)}(y) T_{1k,lm}. */
+static void grad_S(const cplx *S, int L, int l, int m, cplx g[3]) {
+    g[0] = g[1] = g[2] = 0.0;
+    for (int k = -1; k <= 1; k++) {
+        cplx f = Sget(S, L, l - 1, m - k) * Tcoef(1, k, l, m);
+        for (int a = 0; a < 3; a++) g[a] += g1[k + 1][a] * f;
+    }
+}
+
+/* Hessian from the j=2 terms of the translation. */
+static void hess_S(const cplx *S, int L, int l, int m, cplx H[3][3]) {
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) H[a][b] = 0.0;
+    for (int k = -2; k <= 2; k++) {
+        cplx f = Sget(S, L, l - 2, m - k) * Tcoef(2, k, l, m);
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) H[a][b] += h2[k + 2][a][b] * f;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Quaternions (eq. qprule)                                                   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { cplx s, v[3]; } cquat;
+
+static cquat cq_zero(void) { cquat q; q.s = 0; q.v[0] = q.v[1] = q.v[2] = 0; return q; }
+
+static cquat cq_mul(cquat f, cquat g) {
+    cquat r;
+    r.s = f.s * g.s - (f.v[0] * g.v[0] + f.v[1] * g.v[1] + f.v[2] * g.v[2]);
+    r.v[0] = f.s * g.v[0] + g.s * f.v[0] + (f.v[1] * g.v[2] - f.v[2] * g.v[1]);
+    r.v[1] = f.s * g.v[1] + g.s * f.v[1] + (f.v[2] * g.v[0] - f.v[0] * g.v[2]);
+    r.v[2] = f.s * g.v[2] + g.s * f.v[2] + (f.v[0] * g.v[1] - f.v[1] * g.v[0]);
+    return r;
+}
+
+static cquat cq_vec(const cplx v[3]) { cquat q; q.s = 0; q.v[0] = v[0]; q.v[1] = v[1]; q.v[2] = v[2]; return q; }
+static cquat cq_rvec(const double v[3]) { cquat q; q.s = 0; q.v[0] = v[0]; q.v[1] = v[1]; q.v[2] = v[2]; return q; }
+static void cq_axpy(cquat *acc, cplx a, cquat x) {
+    acc->s += a * x.s;
+    for (int i = 0; i < 3; i++) acc->v[i] += a * x.v[i];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dubiner (Koornwinder) basis on T for the node interpolant                  */
+/* ------------------------------------------------------------------------- */
+
+static void dubiner(int deg, double u, double v, double *out) {
+    double x = 2.0 * u - 1.0 + v, w = 1.0 - v, eta = 2.0 * v - 1.0;
+    double Lh[ORC_PMAX + 2];
+    Lh[0] = 1.0;
+    if (deg >= 1) Lh[1] = x;
+    for (int a = 1; a < deg; a++) Lh[a + 1] = ((2 * a + 1) * x * Lh[a] - a * w * w * Lh[a - 1]) / (a + 1);
+    int idx = 0;
+    for (int a = 0; a <= deg; a++) {
+        double al = 2 * a + 1;
+        double J[ORC_PMAX + 2];
+        J[0] = 1.0;
+        if (deg - a >= 1) J[1] = 0.5 * ((al + 2) * eta + al);
+        for (int b = 1; b < deg - a; b++) {
+            double c1 = 2.0 * (b + 1) * (b + al + 1) * (2 * b + al);
+            double c2 = (2 * b + al + 1) * (al * al);
+            double c3 = (2 * b + al) * (2 * b + al + 1) * (2 * b + al + 2);
+            double c4 = 2.0 * (b + al) * b * (2 * b + al + 2);
+            J[b + 1] = ((c2 + c3 * eta) * J[b] - c4 * J[b - 1]) / c1;
+        }
+        for (int b = 0; b <= deg - a; b++) out[idx++] = Lh[a] * J[b];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-order tables                                                           */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int p, np, pt, nup;
+    double rho0;
+    double tq[ORC_PTMAX], wq[ORC_PTMAX];          /* edge GL nodes */
+    double U[ORC_PTMAX * ORC_PTMAX];              /* c~ = U F (inverse Vandermonde) */
+    double tu[2 * ORC_PTMAX], wu[2 * ORC_PTMAX];  /* upsampled GL */
+    double Lup[2 * ORC_PTMAX * ORC_PTMAX];        /* Lagrange of edge nodes at tu */
+    double tom[ORC_NOM], wom[ORC_NOM];            /* GL per Omega_0 panel */
+    double *Eint;                                 /* [3*pt][np] node -> edge GL samples */
+    double *Vint;                                 /* [3][np] node -> vertices */
+} orc_order;
+
+/* edge e parametrisation (u,v)(t), t in [-1,1]: E0 v0->v1, E1 v1->v2, E2 v2->v0 */
+static void edge_uv(int e, double t, double *u, double *v) {
+    double s = 0.5 * (1.0 + t);
+    if (e == 0) { *u = s; *v = 0.0; }
+    else if (e == 1) { *u = 1.0 - s; *v = s; }
+    else { *u = 0.0; *v = 1.0 - s; }
+}
+
+static int order_init(orc_order *O, int p, const double *ref_uv, const orc_opts *opt) {
+    memset(O, 0, sizeof(*O));
+    O->p = p;
+    O->np = p * (p + 1) / 2;
+    O->pt = (opt && opt->ptilde > 0) ? opt->ptilde : 2 * p;
+    if (O->pt > ORC_PTMAX || p > ORC_PMAX || p < 1) return -1;
+    O->nup = 2 * O->pt;
+    O->rho0 = (opt && opt->rho0 > 0) ? opt->rho0 : pow(10.0, 5.0 / O->pt);
+    int pt = O->pt, np = O->np;
+    gauss_legendre(pt, O->tq, O->wq);
+    gauss_legendre(O->nup, O->tu, O->wu);
+    gauss_legendre(ORC_NOM, O->tom, O->wom);
+    /* U = inverse of the monomial Vandermonde [t_q^i] (Sec. 3.4) */
+    double *V = malloc(sizeof(double) * pt * pt);
+    int piv[ORC_PTMAX];
+    for (int q = 0; q < pt; q++)
+        for (int i = 0; i < pt; i++) V[q * pt + i] = pow(O->tq[q], i);
+    for (int i = 0; i < pt * pt; i++) O->U[i] = 0.0;
+    for (int i = 0; i < pt; i++) O->U[i * pt + i] = 1.0;
+    if (lu_factor(pt, V, piv)) { free(V); return -1; }
+    lu_solve(pt, V, piv, pt, O->U);
+    free(V);
+    /* Lagrange basis of the pt edge nodes at the upsampled nodes */
+    for (int s = 0; s < O->nup; s++)
+        for (int q = 0; q < pt; q++) {
+            double L = 1.0;
+            for (int r = 0; r < pt; r++)
+                if (r != q) L *= (O->tu[s] - O->tq[r]) / (O->tq[q] - O->tq[r]);
+            O->Lup[s * pt + q] = L;
+        }
+    /* node interpolant: l_i(u,v) = psi(u,v)^T Vd^{-1}, Vd[i][b] = psi_b(node i) */
+    double *Vd = malloc(sizeof(double) * np * np);
+    int *pv = malloc(sizeof(int) * np);
+    for (int i = 0; i < np; i++) dubiner(p - 1, ref_uv[2 * i], ref_uv[2 * i + 1], Vd + i * np);
+    /* transpose so that we solve Vd^T X = psi(pt) -> X[i] = l_i(pt) */
+    double *VdT = malloc(sizeof(double) * np * np);
+    for (int i = 0; i < np; i++)
+        for (int b = 0; b < np; b++) VdT[b * np + i] = Vd[i * np + b];
+    if (lu_factor(np, VdT, pv)) { free(Vd); free(VdT); free(pv); return -1; }
+    int nsamp = 3 * pt + 3;
+    double *B = malloc(sizeof(double) * np * nsamp);
+    double psi[ORC_PMAX * ORC_PMAX];
+    for (int e = 0; e < 3; e++)
+        for (int q = 0; q < pt; q++) {
+            double u, v;
+            edge_uv(e, O->tq[q], &u, &v);
+            dubiner(p - 1, u, v, psi);
+            for (int b = 0; b < np; b++) B[b * nsamp + e * pt + q] = psi[b];
+        }
+    const double vtx[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+    for (int k = 0; k < 3; k++) {
+        dubiner(p - 1, vtx[k][0], vtx[k][1], psi);
+        for (int b = 0; b < np; b++) B[b * nsamp + 3 * pt + k] = psi[b];
+    }
+    lu_solve(np, VdT, pv, nsamp, B);
+    O->Eint = malloc(sizeof(double) * 3 * pt * np);
+    O->Vint = malloc(sizeof(double) * 3 * np);
+    for (int s = 0; s < 3 * pt; s++)
+        for (int i = 0; i < np; i++) O->Eint[s * np + i] = B[i * nsamp + s];
+    for (int k = 0; k < 3; k++)
+        for (int i = 0; i < np; i++) O->Vint[k * np + i] = B[i * nsamp + 3 * pt + k];
+    free(B); free(Vd); free(VdT); free(pv);
+    return 0;
+}
+
+static void order_free(orc_order *O) {
+    free(O->Eint);
+    free(O->Vint);
+    O->Eint = O->Vint = NULL;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Patch data (source-only Steps 1-3)                                         */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int p, np, pt, nh;       /* nh = (p+1)^2 harmonics of degree <= p */
+    double c[3], R[3][3], s; /* y = s R^T (x - c); R columns e_x, e_y, e_z */
+    double V[3][3];          /* vertices, global */
+    double cP[3], RP, dP;    /* near-list geometry (global) */
+    double *y, *nu;          /* [np][3] local nodes and normals */
+    double *ea;              /* [3][p][3] local Legendre coefficients of the edges */
+    double *ey, *et;         /* [3*pt][3] local edge samples and tangents dy/dt */
+    cplx *eg;                /* [3*pt][nh][3] grad S^{(j,k)} at edge samples */
+    cplx *eh;                /* [3*pt][nh][3] (Hess S^{(j,k)}) tau at edge samples */
+    double *XD, *XSp, *XS1, *XS2; /* fit matrices */
+    double kappa1;           /* (unused placeholder for diagnostics) */
+    int ok;
+} orc_patch;
+
+static void legendre_real(int n, double t, double *P, double *dP) {
+    P[0] = 1.0; dP[0] = 0.0;
+    if (n > 1) { P[1] = t; dP[1] = 1.0; }
+    for (int k = 1; k + 1 < n; k++) {
+        P[k + 1] = ((2 * k + 1) * t * P[k] - k * P[k - 1]) / (k + 1);
+        dP[k + 1] = t * dP[k] + (k + 1) * P[k];
+    }
+}
+
+static void legendre_cplx(int n, cplx t, cplx *P, cplx *dP) {
+    P[0] = 1.0; dP[0] = 0.0;
+    if (n > 1) { P[1] = t; dP[1] = 1.0; }
+    for (int k = 1; k + 1 < n; k++) {
+        P[k + 1] = ((2 * k + 1) * t * P[k] - k * P[k - 1]) / (k + 1);
+        dP[k + 1] = t * dP[k] + (k + 1) * P[k];
+    }
+}
+
+/* edge curve (local coordinates) and its derivative at real t */
+static void edge_eval(const double *ea, int p, double t, double y[3], double dy[3]) {
+    double P[ORC_PMAX], dP[ORC_PMAX];
+    legendre_real(p, t, P, dP);
+    for (int a = 0; a < 3; a++) {
+        y[a] = 0; dy[a] = 0;
+        for (int n = 0; n < p; n++) { y[a] += ea[n * 3 + a] * P[n]; dy[a] += ea[n * 3 + a] * dP[n]; }
+    }
+}
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void patch_free(orc_patch *P) {
+    free(P->y); free(P->nu); free(P->ea); free(P->ey); free(P->et);
+    free(P->eg); free(P->eh);
+    free(P->XD); free(P->XSp); free(P->XS1); free(P->XS2);
+    memset(P, 0, sizeof(*P));
+}
+
+static int patch_setup(orc_patch *P, const orc_order *O, const double *xyz, const double *nrm) {
+    lowdeg_init();
+    memset(P, 0, sizeof(*P));
+    int p = O->p, np = O->np, pt = O->pt;
+    P->p = p; P->np = np; P->pt = pt; P->nh = NHFULL(p);
+    int nh = P->nh;
+    /* vertices and global edge samples through the node interpolant */
+    for (int k = 0; k < 3; k++)
+        for (int a = 0; a < 3; a++) {
+            double s = 0;
+            for (int i = 0; i < np; i++) s += O->Vint[k * np + i] * xyz[3 * i + a];
+            P->V[k][a] = s;
+        }
+    double *gsamp = malloc(sizeof(double) * 3 * pt * 3);
+    for (int sI = 0; sI < 3 * pt; sI++)
+        for (int a = 0; a < 3; a++) {
+            double s = 0;
+            for (int i = 0; i < np; i++) s += O->Eint[sI * np + i] * xyz[3 * i + a];
+            gsamp[sI * 3 + a] = s;
+        }
+    /* frame (Sec. 4 input/output; Sec. 5.1 scaling) */
+    double e01[3], e12[3], e20[3], e02[3], nz[3];
+    for (int a = 0; a < 3; a++) {
+        P->c[a] = (P->V[0][a] + P->V[1][a] + P->V[2][a]) / 3.0;
+        e01[a] = P->V[1][a] - P->V[0][a];
+        e12[a] = P->V[2][a] - P->V[1][a];
+        e20[a] = P->V[0][a] - P->V[2][a];
+        e02[a] = P->V[2][a] - P->V[0][a];
+    }
+    cross3(e01, e02, nz);
+    double nzl = sqrt(dot3(nz, nz));
+    if (!(nzl > 0)) { free(gsamp); return -1; }
+    double L0 = sqrt(dot3(e01, e01)), L1 = sqrt(dot3(e12, e12)), L2 = sqrt(dot3(e20, e20));
+    const double *ex_src = e01;
+    double Lm = L0;
+    if (L1 > Lm) { Lm = L1; ex_src = e12; }
+    if (L2 > Lm) { Lm = L2; ex_src = e20; }
+    double ex[3], ey[3], ez[3];
+    for (int a = 0; a < 3; a++) { ez[a] = nz[a] / nzl; ex[a] = ex_src[a] / Lm; }
+    cross3(ez, ex, ey);
+    for (int a = 0; a < 3; a++) { P->R[a][0] = ex[a]; P->R[a][1] = ey[a]; P->R[a][2] = ez[a]; }
+    P->s = 1.0 / Lm;
+    /* near-list geometry (global): c_P = vertex mean, R_P = max distance to nodes
+       and vertices, d_P = longest edge */
+    for (int a = 0; a < 3; a++) P->cP[a] = P->c[a];
+    P->dP = Lm;
+    double rp = 0;
+    for (int i = 0; i < np; i++) {
+        double d[3] = {xyz[3 * i] - P->cP[0], xyz[3 * i + 1] - P->cP[1], xyz[3 * i + 2] - P->cP[2]};
+        double r = sqrt(dot3(d, d));
+        if (r > rp) rp = r;
+    }
+    for (int k = 0; k < 3; k++) {
+        double d[3] = {P->V[k][0] - P->cP[0], P->V[k][1] - P->cP[1], P->V[k][2] - P->cP[2]};
+        double r = sqrt(dot3(d, d));
+        if (r > rp) rp = r;
+    }
+    P->RP = rp;
+    /* local nodes and normals */
+    P->y = malloc(sizeof(double) * np * 3);
+    P->nu = malloc(sizeof(double) * np * 3);
+    for (int i = 0; i < np; i++)
+        for (int b = 0; b < 3; b++) {
+            double sy = 0, sn = 0;
+            for (int a = 0; a < 3; a++) {
+                sy += P->R[a][b] * (xyz[3 * i + a] - P->c[a]);
+                sn += P->R[a][b] * nrm[3 * i + a];
+            }
+            P->y[3 * i + b] = P->s * sy;
+            P->nu[3 * i + b] = sn;
+        }
+    /* local edge samples, Legendre coefficients a_n = (2n+1)/2 sum_q w_q y(t_q) P_n(t_q) */
+    P->ey = malloc(sizeof(double) * 3 * pt * 3);
+    P->et = malloc(sizeof(double) * 3 * pt * 3);
+    P->ea = malloc(sizeof(double) * 3 * p * 3);
+    for (int sI = 0; sI < 3 * pt; sI++)
+        for (int b = 0; b < 3; b++) {
+            double sy = 0;
+            for (int a = 0; a < 3; a++) sy += P->R[a][b] * (gsamp[3 * sI + a] - P->c[a]);
+            P->ey[3 * sI + b] = P->s * sy;
+        }
+    free(gsamp);
+    for (int e = 0; e < 3; e++) {
+        double *ea = P->ea + e * p * 3;
+        for (int n = 0; n < p * 3; n++) ea[n] = 0.0;
+        for (int q = 0; q < pt; q++) {
+            double Pl[ORC_PMAX], dPl[ORC_PMAX];
+            legendre_real(p, O->tq[q], Pl, dPl);
+            for (int n = 0; n < p; n++)
+                for (int b = 0; b < 3; b++)
+                    ea[n * 3 + b] += 0.5 * (2 * n + 1) * O->wq[q] * P->ey[3 * (e * pt + q) + b] * Pl[n];
+        }
+        for (int q = 0; q < pt; q++) {
+            double yy[3], dy[3];
+            edge_eval(ea, p, O->tq[q], yy, dy);
+            for (int b = 0; b < 3; b++) P->et[3 * (e * pt + q) + b] = dy[b];
+        }
+    }
+    /* Step 3: harmonics at the edge samples */
+    P->eg = malloc(sizeof(cplx) * 3 * pt * nh * 3);
+    P->eh = malloc(sizeof(cplx) * 3 * pt * nh * 3);
+    cplx *S = malloc(sizeof(cplx) * NHFULL(ORC_LMAX));
+    for (int sI = 0; sI < 3 * pt; sI++) {
+        solid_S(p, P->ey + 3 * sI, S);
+        for (int j = 0; j <= p; j++)
+            for (int k = -j; k <= j; k++) {
+                cplx g[3], H[3][3];
+                grad_S(S, p, j, k, g);
+                hess_S(S, p, j, k, H);
+                cplx *gg = P->eg + ((size_t)sI * nh + HIDX(j, k)) * 3;
+                cplx *hh = P->eh + ((size_t)sI * nh + HIDX(j, k)) * 3;
+                const double *tau = P->et + 3 * sI;
+                for (int a = 0; a < 3; a++) {
+                    gg[a] = g[a];
+                    hh[a] = H[a][0] * tau[0] + H[a][1] * tau[1] + H[a][2] * tau[2];
+                }
+            }
+    }
+    /* Steps 1-2 (matrix-build variant): the system of eq. (dlpdensitylinearsystem2) */
+    int n4 = 4 * np;
+    double *F = malloc(sizeof(double) * 3 * np * np); /* F[a][i][lm] */
+    double *Hn = malloc(sizeof(double) * np * np);
+    for (int i = 0; i < np; i++) {
+        solid_S(p, P->y + 3 * i, S);
+        int lm = 0;
+        for (int l = 1; l <= p; l++)
+            for (int m = 1; m <= l; m++, lm++) {
+                cplx g[3];
+                grad_S(S, p, l, m, g);
+                for (int a = 0; a < 3; a++) F[(a * np + i) * np + lm] = sqrt(2.0) * cimag(g[a]);
+                Hn[i * np + lm] = sqrt(2.0) * cimag(S[HIDX(l, m)]);
+            }
+    }
+    free(S);
+    double *A = malloc(sizeof(double) * n4 * n4);
+    memset(A, 0, sizeof(double) * n4 * n4);
+#define AEL(bi, bj, i, j) A[((bi) * np + (i)) * n4 + (bj) * np + (j)]
+#define FEL(a, i, j) F[((a) * np + (i)) * np + (j)]
+    for (int i = 0; i < np; i++)
+        for (int j = 0; j < np; j++) {
+            double f1 = FEL(0, i, j), f2 = FEL(1, i, j), f3 = FEL(2, i, j);
+            AEL(0, 1, i, j) = -f1; AEL(0, 2, i, j) = -f2; AEL(0, 3, i, j) = -f3;
+            AEL(1, 0, i, j) = f1;  AEL(1, 2, i, j) = -f3; AEL(1, 3, i, j) = f2;
+            AEL(2, 0, i, j) = f2;  AEL(2, 1, i, j) = f3;  AEL(2, 3, i, j) = -f1;
+            AEL(3, 0, i, j) = f3;  AEL(3, 1, i, j) = -f2; AEL(3, 2, i, j) = f1;
+        }
+    int *piv = malloc(sizeof(int) * n4);
+    int bad = lu_factor(n4, A, piv);
+    P->XD = malloc(sizeof(double) * n4 * np);
+    P->XSp = malloc(sizeof(double) * n4 * np);
+    memset(P->XD, 0, sizeof(double) * n4 * np);
+    memset(P->XSp, 0, sizeof(double) * n4 * np);
+    for (int i = 0; i < np; i++) {
+        P->XD[i * np + i] = 1.0;                          /* [I;0;0;0] */
+        for (int a = 0; a < 3; a++) P->XSp[((a + 1) * np + i) * np + i] = P->nu[3 * i + a]; /* [0;diag nu] */
+    }
+    if (!bad) {
+        lu_solve(n4, A, piv, np, P->XD);
+        lu_solve(n4, A, piv, np, P->XSp);
+    }
+    /* scalar fit A_S = sum_a F_a diag(nu_a) (eq. slpdensitylinearsystem) */
+    double *AS = malloc(sizeof(double) * np * np);
+    for (int i = 0; i < np; i++)
+        for (int j = 0; j < np; j++)
+            AS[i * np + j] = FEL(0, i, j) * P->nu[3 * i] + FEL(1, i, j) * P->nu[3 * i + 1] + FEL(2, i, j) * P->nu[3 * i + 2];
+    int *pivs = malloc(sizeof(int) * np);
+    int bad2 = lu_factor(np, AS, pivs);
+    P->XS1 = malloc(sizeof(double) * np * np);
+    memset(P->XS1, 0, sizeof(double) * np * np);
+    for (int i = 0; i < np; i++) P->XS1[i * np + i] = 1.0;
+    if (!bad2) lu_solve(np, AS, pivs, np, P->XS1);
+    /* X_S2 = X_D Hn A_S^{-1}: coefficients g of the intermediate density rho = Hn d */
+    double *tmp = malloc(sizeof(double) * np * np);
+    for (int i = 0; i < np; i++)
+        for (int j = 0; j < np; j++) {
+            double s = 0;
+            for (int k = 0; k < np; k++) s += Hn[i * np + k] * P->XS1[k * np + j];
+            tmp[i * np + j] = s;
+        }
+    P->XS2 = malloc(sizeof(double) * n4 * np);
+    for (int r = 0; r < n4; r++)
+        for (int j = 0; j < np; j++) {
+            double s = 0;
+            for (int k = 0; k < np; k++) s += P->XD[r * np + k] * tmp[k * np + j];
+            P->XS2[r * np + j] = s;
+        }
+#undef AEL
+#undef FEL
+    free(tmp); free(AS); free(pivs); free(A); free(piv); free(F); free(Hn);
+    P->ok = !(bad || bad2);
+    return P->ok ? 0 : -2;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step 5: root t0, SSQ moments, modified weights                             */
+/* ------------------------------------------------------------------------- */
+
+/* Newton on sum_a (y_a(t) - y'_a)^2 = 0 in complex t, started from the root of
+ * the straight chord; Im t0 >= 0 is returned (roots come in conjugate pairs). */
+static int edge_root(const double *ea, int p, const double yt[3], int maxit, cplx *t0) {
+    double ym[3], yp[3], d1[3], d2[3];
+    edge_eval(ea, p, -1.0, ym, d1);
+    edge_eval(ea, p, 1.0, yp, d2);
+    double c[3], b[3], w[3], bw[3];
+    for (int a = 0; a < 3; a++) { c[a] = 0.5 * (yp[a] + ym[a]); b[a] = 0.5 * (yp[a] - ym[a]); w[a] = yt[a] - c[a]; }
+    cross3(b, w, bw);
+    double bb = dot3(b, b);
+    cplx t = (dot3(b, w) + I * sqrt(dot3(bw, bw))) / bb;
+    int conv = 0;
+    for (int it = 0; it < maxit; it++) {
+        cplx P[ORC_PMAX], dP[ORC_PMAX];
+        legendre_cplx(p, t, P, dP);
+        cplx g = 0, gp = 0;
+        for (int a = 0; a < 3; a++) {
+            cplx y = 0, dy = 0;
+            for (int n = 0; n < p; n++) { y += ea[n * 3 + a] * P[n]; dy += ea[n * 3 + a] * dP[n]; }
+            cplx r = y - yt[a];
+            g += r * r;
+            gp += 2.0 * r * dy;
+        }
+        if (gp == 0.0) break;
+        cplx dt = g / gp;
+        t -= dt;
+        double at = cabs(t);
+        if (cabs(dt) <= 1e-14 * (at > 1.0 ? at : 1.0)) { conv = 1; break; }
+    }
+    if (cimag(t) < 0) t = conj(t);
+    *t0 = t;
+    return conv;
+}
+
+/* Bernstein-ellipse radius of z with respect to [-1,1] */
+static double bernstein_rho(cplx z) {
+    cplx w = z + csqrt(z - 1.0) * csqrt(z + 1.0);
+    double r = cabs(w);
+    return r >= 1.0 ? r : 1.0 / r;
+}
+
+/* Moments I_i = int_{-1}^{1} t^i / ((t-t0)(t-conj t0))^{m/2} dt, m = 1 and 3,
+ * by the recurrences obtained from integration by parts (Sec. 2.4). */
+static void ssq_moments(int n, double a, double b, double *J, double *K) {
+    double c0 = a * a + b * b;
+    double sp = sqrt((1 - a) * (1 - a) + b * b), sm = sqrt((1 + a) * (1 + a) + b * b);
+    J[0] = asinh((1 - a) / b) + asinh((1 + a) / b);
+    if (n > 1) J[1] = (sp - sm) + a * J[0];
+    for (int i = 2; i < n; i++) {
+        double br = sp - ((i - 1) % 2 ? -sm : sm);
+        J[i] = (br + (2 * i - 1) * a * J[i - 1] - (i - 1) * c0 * J[i - 2]) / i;
+    }
+    if (K) {
+        K[0] = ((1 - a) / sp + (1 + a) / sm) / (b * b);
+        if (n > 1) K[1] = (-1.0 / sp + 1.0 / sm) + a * K[0];
+        for (int i = 0; i + 2 < n; i++) K[i + 2] = J[i] + 2 * a * K[i + 1] - c0 * K[i];
+    }
+}
+
+/* Modified weights om[m-index][q] on one edge such that
+ * int_{-1}^{1} f(t)/|y(t)-y'|^m dt ~ sum_q om[q] f(t_q) for smooth f. */
+static void edge_weights(const orc_order *O, const double *ea, int p, const double *eyq,
+                         const double yt[3], cplx t0, int use_ssq, int want3,
+                         double *om1, double *om3) {
+    int pt = O->pt;
+    if (use_ssq) {
+        double a = creal(t0), b = cimag(t0);
+        double J[ORC_PTMAX], K[ORC_PTMAX];
+        ssq_moments(pt, a, b, J, want3 ? K : NULL);
+        for (int q = 0; q < pt; q++) {
+            double l1 = 0, l3 = 0;
+            for (int i = 0; i < pt; i++) {
+                l1 += O->U[i * pt + q] * J[i];
+                if (want3) l3 += O->U[i * pt + q] * K[i];
+            }
+            double d[3] = {yt[0] - eyq[3 * q], yt[1] - eyq[3 * q + 1], yt[2] - eyq[3 * q + 2]};
+            double rq = sqrt(dot3(d, d));
+            double ratio = cabs(O->tq[q] - t0) / rq;
+            om1[q] = l1 * ratio;
+            if (want3) om3[q] = l3 * ratio * ratio * ratio;
+        }
+    } else {
+        for (int q = 0; q < pt; q++) { om1[q] = 0; if (want3) om3[q] = 0; }
+        for (int s = 0; s < O->nup; s++) {
+            double y[3], dy[3];
+            edge_eval(ea, p, O->tu[s], y, dy);
+            double d[3] = {yt[0] - y[0], yt[1] - y[1], yt[2] - y[2]};
+            double r = sqrt(dot3(d, d));
+            double k1 = O->wu[s] / r, k3 = k1 / (r * r);
+            for (int q = 0; q < pt; q++) {
+                om1[q] += k1 * O->Lup[s * pt + q];
+                if (want3) om3[q] += k3 * O->Lup[s * pt + q];
+            }
+        }
+    }
+}
+
+/* Omega_0 (eq. solidangle) and d Omega_0 / d nu' (eq. dprimelineintegrals) on one
+ * edge by Gauss-Legendre panels graded geometrically toward Re t0. */
+static void omega0_edge(const orc_order *O, const double *ea, int p, const double yt[3],
+                        const double u[3], cplx t0, int have_root, const double *nut,
+                        double *Om0, double *dOm0) {
+    double c, sig;
+    if (have_root) {
+        c = creal(t0);
+        if (c < -1) c = -1;
+        if (c > 1) c = 1;
+        sig = cabs(t0 - c);
+        if (sig < 1e-14) sig = 1e-14;
+    } else { c = 0; sig = 4.0; }
+    double br[256];
+    int nb = 0;
+    /* breakpoints: left side descending, then inner panel, right side */
+    double left[128], right[128];
+    int nl = 0, nr = 0;
+    double lo = c - 0.5 * sig, hi = c + 0.5 * sig;
+    if (lo < -1) lo = -1;
+    if (hi > 1) hi = 1;
+    double x = hi, len = sig;
+    while (x < 1.0 && nr < 127) { double nx = x + len; if (nx > 1) nx = 1; right[nr++] = nx; x = nx; len *= 2; }
+    x = lo; len = sig;
+    while (x > -1.0 && nl < 127) { double nx = x - len; if (nx < -1) nx = -1; left[nl++] = nx; x = nx; len *= 2; }
+    for (int i = nl - 1; i >= 0; i--) br[nb++] = left[i];
+    br[nb++] = lo;
+    br[nb++] = hi;
+    for (int i = 0; i < nr; i++) br[nb++] = right[i];
+    double s0 = 0, s1 = 0;
+    for (int k = 0; k + 1 < nb; k++) {
+        double a0 = br[k], a1 = br[k + 1];
+        if (!(a1 > a0)) continue;
+        double mid = 0.5 * (a0 + a1), half = 0.5 * (a1 - a0);
+        for (int g = 0; g < ORC_NOM; g++) {
+            double t = mid + half * O->tom[g];
+            double y[3], tau[3];
+            edge_eval(ea, p, t, y, tau);
+            double d[3] = {yt[0] - y[0], yt[1] - y[1], yt[2] - y[2]};
+            double r = sqrt(dot3(d, d));
+            double E = r + dot3(u, d);
+            double dxu[3];
+            cross3(d, u, dxu);
+            double N = dot3(dxu, tau);
+            double wgt = half * O->wom[g];
+            s0 -= wgt * N / (r * E);
+            if (dOm0) {
+                double nxu[3];
+                cross3(nut, u, nxu);
+                double nd = dot3(nut, d), nu_u = dot3(nut, u);
+                double v = dot3(nxu, tau) / (r * E) - nu_u * N / (r * E * E) - nd * N / (r * r * E * E)
+                           - nd * N / (r * r * r * E);
+                s1 -= wgt * v;
+            }
+        }
+    }
+    *Om0 += s0;
+    if (dOm0) *dOm0 += s1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Steps 4-8 for one (target, patch) pair                                     */
+/* ------------------------------------------------------------------------- */
+
+/* Quantities of Steps 4-7 for one pair: per lm (1<=m<=l<=p, lm = l(l-1)/2+m-1)
+ * B[lm][4] = int over dP of beta^{(l,m)} (Thm. dlp1form, eq. dlp1formrep2),
+ * Psi[lm]  = int over dP of psi^{(l,m)} (Thm. cslp1form),
+ * Bd[lm][4] = d B / d nu' (Sec. 3.7), Om = (Omega_0, Omega), dOm = d Om / d nu'. */
+typedef struct {
+    double B[ORC_PMAX * (ORC_PMAX + 1) / 2][4];
+    double Bd[ORC_PMAX * (ORC_PMAX + 1) / 2][4];
+    double Psi[ORC_PMAX * (ORC_PMAX + 1) / 2];
+    double Om[4], dOm[4];
+    double yt[3], nut[3];
+    int flags;
+} orc_forms;
+
+static int pair_forms(const orc_order *O, const orc_patch *P, const orc_opts *opt,
+                      const double xt[3], const double nt[3], int self_i, int want_dp, orc_forms *F) {
+    int p = P->p, np = P->np, pt = P->pt, nh = P->nh;
+    int flags = 0;
+    /* target in local coordinates */
+    double *yt = F->yt, *nut = F->nut;
+    for (int b = 0; b < 3; b++) {
+        double sy = 0, sn = 0;
+        for (int a = 0; a < 3; a++) { sy += P->R[a][b] * (xt[a] - P->c[a]); sn += P->R[a][b] * nt[a]; }
+        yt[b] = P->s * sy;
+        nut[b] = sn;
+    }
+    /* Step 4: harmonics at the target */
+    cplx St[NHFULL(ORC_PMAX)];
+    solid_S(p, yt, St);
+    cplx gSt[NHFULL(ORC_PMAX)][3];
+    cplx HSt[NHFULL(ORC_PMAX)][3][3];
+    for (int l = 0; l <= p; l++)
+        for (int m = -l; m <= l; m++) {
+            grad_S(St, p, l, m, gSt[HIDX(l, m)]);
+            if (want_dp) hess_S(St, p, l, m, HSt[HIDX(l, m)]);
+        }
+    /* choice of u (Thm. dlp1form) */
+    double u[3] = {0, 0, 1};
+    {
+        double mplus = 2, mminus = 2;
+        for (int s = 0; s < np + 3 * pt; s++) {
+            const double *r = s < np ? P->y + 3 * s : P->ey + 3 * (s - np);
+            double d[3] = {yt[0] - r[0], yt[1] - r[1], yt[2] - r[2]};
+            double dl = sqrt(dot3(d, d));
+            if (dl == 0.0) continue;
+            double cz = d[2] / dl;
+            if (cz < mplus) mplus = cz;
+            if (-cz < mminus) mminus = -cz;
+        }
+        if (self_i < 0 && mminus > mplus) u[2] = -1;
+        double best = (u[2] > 0) ? mplus : mminus;
+        if (best < -0.5) flags |= FLAG_UPOOR;
+    }
+    /* Steps 5-6: per-edge root, weights, line integrals (eqs. lineintegrals, solidangle,
+       dprimelineintegrals) */
+    static __thread cquat Q[NHFULL(ORC_PMAX)], dQ[NHFULL(ORC_PMAX)];
+    cplx V[NHFULL(ORC_PMAX)];
+    double Om0 = 0, dOm0 = 0, Omv[3] = {0, 0, 0}, dOmv[3] = {0, 0, 0};
+    for (int h = 0; h < nh; h++) { Q[h] = cq_zero(); dQ[h] = cq_zero(); V[h] = 0; }
+    for (int e = 0; e < 3; e++) {
+        const double *ea = P->ea + e * p * 3;
+        cplx t0;
+        int conv = edge_root(ea, p, yt, (opt && opt->newton_max > 0) ? opt->newton_max : 30, &t0);
+        if (!conv) flags |= FLAG_NEWTON;
+        if (conv && cimag(t0) < 1e-14 && fabs(creal(t0)) <= 1.0) flags |= FLAG_ONEDGE;
+        int use_ssq = conv && bernstein_rho(t0) < O->rho0 && cimag(t0) > 0;
+        double om1[ORC_PTMAX], om3[ORC_PTMAX];
+        edge_weights(O, ea, p, P->ey + 3 * e * pt, yt, t0, use_ssq, want_dp, om1, om3);
+        omega0_edge(O, ea, p, yt, u, t0, conv, nut, &Om0, want_dp ? &dOm0 : NULL);
+        for (int q = 0; q < pt; q++) {
+            int sI = e * pt + q;
+            const double *yq = P->ey + 3 * sI, *tau = P->et + 3 * sI;
+            double d[3] = {yt[0] - yq[0], yt[1] - yq[1], yt[2] - yq[2]};
+            cquat qd = cq_rvec(d);
+            cquat qn = cq_rvec(nut);
+            double nd = dot3(nut, d);
+            for (int a = 0; a < 3; a++) {
+                Omv[a] -= om1[q] * tau[a];
+                if (want_dp) dOmv[a] += om3[q] * nd * tau[a];
+            }
+            for (int j = 1; j <= p; j++)
+                for (int k = -j; k <= j; k++) {
+                    int h = HIDX(j, k);
+                    const cplx *g = P->eg + ((size_t)sI * nh + h) * 3;
+                    /* V^{jk}: ((r'-r) x grad S^{(j,k)}) . dr / |r'-r| */
+                    cplx cx0 = d[1] * g[2] - d[2] * g[1];
+                    cplx cx1 = d[2] * g[0] - d[0] * g[2];
+                    cplx cx2 = d[0] * g[1] - d[1] * g[0];
+                    V[h] += om1[q] * (cx0 * tau[0] + cx1 * tau[1] + cx2 * tau[2]);
+                    if (j >= 2) {
+                        /* Q^{jk}: (0, (r'-r)/|r'-r|)(0, d grad S^{(j,k)}), eq. (qjkdef2) */
+                        const cplx *hh = P->eh + ((size_t)sI * nh + h) * 3;
+                        cquat qh = cq_vec(hh);
+                        cquat prod = cq_mul(qd, qh);
+                        cq_axpy(&Q[h], om1[q], prod);
+                        if (want_dp) {
+                            cq_axpy(&dQ[h], om1[q], cq_mul(qn, qh));
+                            cq_axpy(&dQ[h], -om3[q] * nd, prod);
+                        }
+                    }
+                }
+        }
+    }
+    F->Om[0] = Om0; F->dOm[0] = dOm0;
+    for (int a = 0; a < 3; a++) { F->Om[a + 1] = Omv[a]; F->dOm[a + 1] = dOmv[a]; }
+    /* Step 7: translations (eqs. cdlp1dintegral, cslp1formrep) and I[gamma] */
+    const double inv4pi = 1.0 / (4.0 * M_PI), sq2 = sqrt(2.0);
+    int lm = 0;
+    for (int l = 1; l <= p; l++)
+        for (int m = 1; m <= l; m++, lm++) {
+            cquat Ib = cq_zero(), dIb = cq_zero();
+            cplx Ip = 0;
+            for (int j = 1; j <= l; j++)
+                for (int k = -j; k <= j; k++) {
+                    double T = Tcoef(j, k, l, m);
+                    if (T == 0.0) continue;
+                    cplx Sv = Sget(St, p, l - j, m - k);
+                    Ip += Dcoef(j, l) * V[HIDX(j, k)] * Sv * T;
+                    if (j >= 2) {
+                        double C = Ccoef(j, l);
+                        cq_axpy(&Ib, C * Sv * T, Q[HIDX(j, k)]);
+                        if (want_dp) {
+                            cplx dS = 0;
+                            if (abs(m - k) <= l - j) {
+                                const cplx *gg = gSt[HIDX(l - j, m - k)];
+                                dS = gg[0] * nut[0] + gg[1] * nut[1] + gg[2] * nut[2];
+                            }
+                            cq_axpy(&dIb, C * Sv * T, dQ[HIDX(j, k)]);
+                            cq_axpy(&dIb, C * dS * T, Q[HIDX(j, k)]);
+                        }
+                    }
+                }
+            /* I[gamma] = (1/4pi) Omega (0, grad S(r')), eq. (gammalmdef) */
+            cquat Om;
+            Om.s = Om0;
+            for (int a = 0; a < 3; a++) Om.v[a] = Omv[a];
+            cquat Ig = cq_mul(Om, cq_vec(gSt[HIDX(l, m)]));
+            F->B[lm][0] = sq2 * cimag(inv4pi * (Ib.s + Ig.s));
+            for (int a = 0; a < 3; a++) F->B[lm][a + 1] = sq2 * cimag(inv4pi * (Ib.v[a] + Ig.v[a]));
+            F->Psi[lm] = sq2 * cimag(inv4pi * (Ip + St[HIDX(l, m)] * Om0));
+            if (want_dp) {
+                cquat dOm;
+                dOm.s = dOm0;
+                for (int a = 0; a < 3; a++) dOm.v[a] = dOmv[a];
+                cplx Hn[3];
+                for (int a = 0; a < 3; a++)
+                    Hn[a] = HSt[HIDX(l, m)][a][0] * nut[0] + HSt[HIDX(l, m)][a][1] * nut[1] + HSt[HIDX(l, m)][a][2] * nut[2];
+                cquat dIg = cq_mul(dOm, cq_vec(gSt[HIDX(l, m)]));
+                cquat dIg2 = cq_mul(Om, cq_vec(Hn));
+                F->Bd[lm][0] = sq2 * cimag(inv4pi * (dIb.s + dIg.s + dIg2.s));
+                for (int a = 0; a < 3; a++) F->Bd[lm][a + 1] = sq2 * cimag(inv4pi * (dIb.v[a] + dIg.v[a] + dIg2.v[a]));
+            }
+        }
+    F->flags = flags;
+    return flags;
+}
+
+/* rows: [4][np] for S, D, S', D' (entries of kernels in mask written).
+ * Returns flag bits. self_i = local node index of the target in the patch or -1. */
+static int pair_rows(const orc_order *O, const orc_patch *P, const orc_opts *opt,
+                     const double xt[3], const double nt[3], int self_i, unsigned mask,
+                     const double *xyz, const double *nrm, const double *wts, double *rows) {
+    int p = P->p, np = P->np;
+    orc_forms F;
+    int flags = pair_forms(O, P, opt, xt, nt, self_i, (mask & ORC_DP) != 0, &F);
+    const double *nut = F.nut;
+    const double inv4pi = 1.0 / (4.0 * M_PI);
+    double *rS = rows, *rD = rows + np, *rSp = rows + 2 * np, *rDp = rows + 3 * np;
+    double L = 1.0 / P->s;
+    for (int i = 0; i < 4 * np; i++) rows[i] = 0;
+    /* Step 8, matrix-build variant: row = [w^T A^{-1}]_0 */
+    int lm = 0;
+    for (int l = 1; l <= p; l++)
+        for (int m = 1; m <= l; m++, lm++) {
+            const double *B = F.B[lm], *Bd = F.Bd[lm];
+            double Psi = F.Psi[lm];
+            double nB = nut[0] * B[1] + nut[1] * B[2] + nut[2] * B[3];
+            double nxB[3];
+            cross3(nut, B + 1, nxB);
+            for (int i = 0; i < np; i++) {
+                double xd[4], w[4], g[4];
+                for (int c = 0; c < 4; c++) {
+                    xd[c] = P->XD[(size_t)(c * np + lm) * np + i];
+                    w[c] = P->XSp[(size_t)(c * np + lm) * np + i];
+                    g[c] = P->XS2[(size_t)(c * np + lm) * np + i];
+                }
+                /* D = -sum_lm [B c]_0 (eq. dlp1formrep) */
+                if (mask & ORC_D) rD[i] -= B[0] * xd[0] - B[1] * xd[1] - B[2] * xd[2] - B[3] * xd[3];
+                /* D' = d/d nu' of the D expression, scaled back by s (Sec. 3.7) */
+                if (mask & ORC_DP) rDp[i] -= P->s * (Bd[0] * xd[0] - Bd[1] * xd[1] - Bd[2] * xd[2] - Bd[3] * xd[3]);
+                /* S' = -[(0,nu') sum B w]_0 with (0, sigma nu) fitted (Sec. 3.6) */
+                if (mask & ORC_SP)
+                    rSp[i] += nB * w[0] + (B[0] * nut[0] + nxB[0]) * w[1] + (B[0] * nut[1] + nxB[1]) * w[2]
+                              + (B[0] * nut[2] + nxB[2]) * w[3];
+                /* S = sum Psi d - [B g]_0 (eq. slp1formrep), scaled back by L */
+                if (mask & ORC_S)
+                    rS[i] += L * (Psi * P->XS1[(size_t)lm * np + i] - (B[0] * g[0] - B[1] * g[1] - B[2] * g[2] - B[3] * g[3]));
+            }
+        }
+    /* jump to the principal value on self pairs; smooth-rule subtraction */
+    if (self_i >= 0) {
+        if (mask & ORC_D) rD[self_i] -= 0.5;
+        if (mask & ORC_SP) rSp[self_i] += 0.5;
+    }
+    for (int i = 0; i < np; i++) {
+        if (i == self_i) continue;
+        const double *xs = xyz + 3 * i, *ns = nrm + 3 * i;
+        double d[3] = {xt[0] - xs[0], xt[1] - xs[1], xt[2] - xs[2]};
+        double r2 = dot3(d, d), r = sqrt(r2), r3 = r2 * r;
+        double w = wts[i];
+        if (mask & ORC_S) rS[i] -= w * inv4pi / r;
+        if (mask & ORC_D) rD[i] -= w * inv4pi * dot3(d, ns) / r3;
+        if (mask & ORC_SP) rSp[i] += w * inv4pi * dot3(d, nt) / r3;
+        if (mask & ORC_DP) rDp[i] -= w * inv4pi * (dot3(nt, ns) / r3 - 3.0 * dot3(d, ns) * dot3(d, nt) / (r3 * r2));
+    }
+    return flags;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported API (ctypes)                                                      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int npatch;
+    const int32_t *order;
+    const int64_t *node_off;
+    const double *xyz, *nrm, *wts;
+    const double *ref_uv[ORC_PMAX + 1];
+    orc_opts opt;
+    orc_order ord[ORC_PMAX + 1];
+    int have[ORC_PMAX + 1];
+} orc_surface;
+
+void *orc_surface_create(int npatch, const int32_t *order, const int64_t *node_off,
+                         const double *xyz, const double *nrm, const double *wts,
+                         const double **ref_uv /*[ORC_PMAX+1]*/, const orc_opts *opt) {
+    binom_init();
+    lowdeg_init();
+    orc_surface *S = calloc(1, sizeof(orc_surface));
+    S->npatch = npatch; S->order = order; S->node_off = node_off;
+    S->xyz = xyz; S->nrm = nrm; S->wts = wts;
+    if (opt) S->opt = *opt;
+    for (int p = 0; p <= ORC_PMAX; p++) S->ref_uv[p] = ref_uv[p];
+    for (int P = 0; P < npatch; P++) {
+        int p = order[P];
+        if (p < 1 || p > ORC_PMAX || !ref_uv[p]) { free(S); return NULL; }
+        if (!S->have[p]) {
+            if (order_init(&S->ord[p], p, ref_uv[p], &S->opt)) { free(S); return NULL; }
+            S->have[p] = 1;
+        }
+    }
+    return S;
+}
+
+void orc_surface_destroy(void *h) {
+    orc_surface *S = h;
+    if (!S) return;
+    for (int p = 0; p <= ORC_PMAX; p++)
+        if (S->have[p]) order_free(&S->ord[p]);
+    free(S);
+}
+
+static int setup_patch_of(const orc_surface *S, int P, orc_patch *pd) {
+    int p = S->order[P];
+    int64_t o = S->node_off[P];
+    return patch_setup(pd, &S->ord[p], S->xyz + 3 * o, S->nrm + 3 * o);
+}
+
+/* Near test (global coordinates): |x_t - c_P| <= R_P + eta d_P, self always. */
+static int is_near(const orc_patch *pd, const double *xt, double eta) {
+    double d[3] = {xt[0] - pd->cP[0], xt[1] - pd->cP[1], xt[2] - pd->cP[2]};
+    return sqrt(dot3(d, d)) <= pd->RP + eta * pd->dP;
+}
+
+/* Geometry of every patch (c_P, R_P, d_P) -> out[npatch][5]. */
+int orc_patch_bounds(void *h, double *out) {
+    orc_surface *S = h;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
+    for (int P = 0; P < S->npatch; P++) {
+        orc_patch pd;
+        /* cheap: only the interpolated vertices and nodes are needed here */
+        int p = S->order[P];
+        const orc_order *O = &S->ord[p];
+        int64_t o = S->node_off[P];
+        const double *xyz = S->xyz + 3 * o;
+        memset(&pd, 0, sizeof(pd));
+        double V[3][3];
+        for (int k = 0; k < 3; k++)
+            for (int a = 0; a < 3; a++) {
+                double s = 0;
+                for (int i = 0; i < O->np; i++) s += O->Vint[k * O->np + i] * xyz[3 * i + a];
+                V[k][a] = s;
+            }
+        double c[3], L = 0;
+        for (int a = 0; a < 3; a++) c[a] = (V[0][a] + V[1][a] + V[2][a]) / 3.0;
+        for (int k = 0; k < 3; k++) {
+            double e[3] = {V[(k + 1) % 3][0] - V[k][0], V[(k + 1) % 3][1] - V[k][1], V[(k + 1) % 3][2] - V[k][2]};
+            double l = sqrt(dot3(e, e));
+            if (l > L) L = l;
+        }
+        double rp = 0;
+        for (int i = 0; i < O->np; i++) {
+            double d[3] = {xyz[3 * i] - c[0], xyz[3 * i + 1] - c[1], xyz[3 * i + 2] - c[2]};
+            double r = sqrt(dot3(d, d));
+            if (r > rp) rp = r;
+        }
+        for (int k = 0; k < 3; k++) {
+            double d[3] = {V[k][0] - c[0], V[k][1] - c[1], V[k][2] - c[2]};
+            double r = sqrt(dot3(d, d));
+            if (r > rp) rp = r;
+        }
+        out[5 * P] = c[0]; out[5 * P + 1] = c[1]; out[5 * P + 2] = c[2];
+        out[5 * P + 3] = rp; out[5 * P + 4] = L;
+        (void)pd;
+    }
+    return err;
+}
+
+/* Near lists for the targets in tsel[nsel] by brute force over all patches.
+ * Pass 1 (pairs == NULL): counts[nsel].  Pass 2: pairs filled row by row with
+ * ascending patch ids (offsets = exclusive scan of counts). */
+int orc_near(void *h, int64_t nsel, const int64_t *tsel, const double *txyz, const int64_t *tself,
+             int64_t *counts, const int64_t *offs, int32_t *pairs) {
+    orc_surface *S = h;
+    double eta = S->opt.eta > 0 ? S->opt.eta : 1.0;
+    double *bd = malloc(sizeof(double) * 5 * S->npatch);
+    orc_patch_bounds(h, bd);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < nsel; r++) {
+        int64_t t = tsel[r];
+        const double *xt = txyz + 3 * t;
+        int64_t cnt = 0;
+        int64_t sn = tself ? tself[t] : -1;
+        for (int P = 0; P < S->npatch; P++) {
+            double d[3] = {xt[0] - bd[5 * P], xt[1] - bd[5 * P + 1], xt[2] - bd[5 * P + 2]};
+            int nearp = sqrt(dot3(d, d)) <= bd[5 * P + 3] + eta * bd[5 * P + 4];
+            if (sn >= S->node_off[P] && sn < S->node_off[P + 1]) nearp = 1;
+            if (nearp) {
+                if (pairs) pairs[offs[r] + cnt] = P;
+                cnt++;
+            }
+        }
+        if (!pairs) counts[r] = cnt;
+    }
+    free(bd);
+    (void)is_near;
+    return 0;
+}
+
+/* Correction rows for explicit pairs.  pair_t[npair] (target index), pair_P[npair]
+ * (patch).  vals: for kernel slot k (S, D, S', D' = 0..3) rows are written at
+ * vals[k][val_off[n] .. + n_p).  flags[npair]. */
+int orc_rows(void *h, int64_t npair, const int64_t *pair_t, const int32_t *pair_P,
+             const double *txyz, const double *tnrm, const int64_t *tself, unsigned mask,
+             const int64_t *val_off, double *valS, double *valD, double *valSp, double *valDp,
+             int32_t *flags) {
+    orc_surface *S = h;
+    /* group pairs by patch: order by patch id (counting sort) */
+    int64_t *cnt = calloc(S->npatch + 1, sizeof(int64_t));
+    for (int64_t n = 0; n < npair; n++) cnt[pair_P[n] + 1]++;
+    for (int P = 0; P < S->npatch; P++) cnt[P + 1] += cnt[P];
+    int64_t *ord = malloc(sizeof(int64_t) * (npair > 0 ? npair : 1));
+    int64_t *fill = malloc(sizeof(int64_t) * (S->npatch + 1));
+    memcpy(fill, cnt, sizeof(int64_t) * (S->npatch + 1));
+    for (int64_t n = 0; n < npair; n++) ord[fill[pair_P[n]]++] = n;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int P = 0; P < S->npatch; P++) {
+        if (cnt[P + 1] == cnt[P]) continue;
+        orc_patch pd;
+        if (setup_patch_of(S, P, &pd)) err |= 1;
+        int p = S->order[P];
+        const orc_order *O = &S->ord[p];
+        int np = O->np;
+        int64_t o = S->node_off[P];
+        double rows[4 * ORC_PMAX * (ORC_PMAX + 1) / 2];
+        for (int64_t k = cnt[P]; k < cnt[P + 1]; k++) {
+            int64_t n = ord[k];
+            int64_t t = pair_t[n];
+            int self_i = -1;
+            if (tself && tself[t] >= o && tself[t] < o + np) self_i = (int)(tself[t] - o);
+            int f = pair_rows(O, &pd, &S->opt, txyz + 3 * t, tnrm + 3 * t, self_i, mask,
+                              S->xyz + 3 * o, S->nrm + 3 * o, S->wts + o, rows);
+            if (flags) flags[n] = f | (pd.ok ? 0 : FLAG_SINGULAR);
+            int64_t vo = val_off[n];
+            for (int i = 0; i < np; i++) {
+                if ((mask & ORC_S) && valS) valS[vo + i] = rows[i];
+                if ((mask & ORC_D) && valD) valD[vo + i] = rows[np + i];
+                if ((mask & ORC_SP) && valSp) valSp[vo + i] = rows[2 * np + i];
+                if ((mask & ORC_DP) && valDp) valDp[vo + i] = rows[3 * np + i];
+            }
+        }
+        patch_free(&pd);
+    }
+    free(cnt); free(ord); free(fill);
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Internals exported for the oracle's own pin tests                          */
+/* ------------------------------------------------------------------------- */
+
+int orc_solid_S(int L, const double *y, double *out /*[(L+1)^2][2]*/) {
+    binom_init();
+    if (L > ORC_LMAX) return -1;
+    cplx S[NHFULL(ORC_LMAX)];
+    solid_S(L, y, S);
+    for (int i = 0; i < NHFULL(L); i++) { out[2 * i] = creal(S[i]); out[2 * i + 1] = cimag(S[i]); }
+    return 0;
+}
+
+int orc_solid_R(int L, const double *xyz, double *out) {
+    binom_init();
+    if (L > ORC_LMAX) return -1;
+    cplx R[NHFULL(ORC_LMAX)];
+    solid_R(L, xyz[0], xyz[1], xyz[2], R);
+    for (int i = 0; i < NHFULL(L); i++) { out[2 * i] = creal(R[i]); out[2 * i + 1] = cimag(R[i]); }
+    return 0;
+}
+
+/* grad and Hessian of S^{(l,m)} at y: g[3][2], H[3][3][2] */
+int orc_grad_hess_S(int L, const double *y, int l, int m, double *g, double *H) {
+    lowdeg_init();
+    cplx S[NHFULL(ORC_LMAX)];
+    solid_S(L, y, S);
+    cplx gg[3], HH[3][3];
+    grad_S(S, L, l, m, gg);
+    hess_S(S, L, l, m, HH);
+    for (int a = 0; a < 3; a++) {
+        g[2 * a] = creal(gg[a]); g[2 * a + 1] = cimag(gg[a]);
+        for (int b = 0; b < 3; b++) { H[2 * (3 * a + b)] = creal(HH[a][b]); H[2 * (3 * a + b) + 1] = cimag(HH[a][b]); }
+    }
+    return 0;
+}
+
+double orc_T(int j, int k, int l, int m) { binom_init(); return Tcoef(j, k, l, m); }
+
+int orc_gauss_legendre(int n, double *x, double *w) { gauss_legendre(n, x, w); return 0; }
+
+int orc_ssq_moments(int n, double a, double b, double *J, double *K) { ssq_moments(n, a, b, J, K); return 0; }
+
+int orc_bernstein_rho(double re, double im, double *rho) { *rho = bernstein_rho(re + I * im); return 0; }
+
+int orc_lu_solve(int n, const double *A, int nrhs, double *B) {
+    double *a = malloc(sizeof(double) * n * n);
+    int *piv = malloc(sizeof(int) * n);
+    memcpy(a, A, sizeof(double) * n * n);
+    int r = lu_factor(n, a, piv);
+    if (!r) lu_solve(n, a, piv, nrhs, B);
+    free(a); free(piv);
+    return r;
+}
+
+/* Patch internals for tests: frame[13] = c, R (row-major), s; vertices[9];
+ * y[np*3]; ea[3*p*3]; ey[3*pt*3]; et[3*pt*3]; XD, XSp [4np*np], XS1 [np*np], XS2 [4np*np]. */
+int orc_patch_internals(void *h, int P, double *frame, double *vert, double *y, double *ea,
+                        double *ey, double *et, double *XD, double *XSp, double *XS1, double *XS2) {
+    orc_surface *S = h;
+    orc_patch pd;
+    int r = setup_patch_of(S, P, &pd);
+    int np = pd.np, pt = pd.pt, p = pd.p;
+    if (frame) {
+        for (int a = 0; a < 3; a++) frame[a] = pd.c[a];
+        for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) frame[3 + 3 * a + b] = pd.R[a][b];
+        frame[12] = pd.s;
+    }
+    if (vert) for (int k = 0; k < 3; k++) for (int a = 0; a < 3; a++) vert[3 * k + a] = pd.V[k][a];
+    if (y) memcpy(y, pd.y, sizeof(double) * np * 3);
+    if (ea) memcpy(ea, pd.ea, sizeof(double) * 3 * p * 3);
+    if (ey) memcpy(ey, pd.ey, sizeof(double) * 3 * pt * 3);
+    if (et) memcpy(et, pd.et, sizeof(double) * 3 * pt * 3);
+    if (XD) memcpy(XD, pd.XD, sizeof(double) * 4 * np * np);
+    if (XSp) memcpy(XSp, pd.XSp, sizeof(double) * 4 * np * np);
+    if (XS1) memcpy(XS1, pd.XS1, sizeof(double) * np * np);
+    if (XS2) memcpy(XS2, pd.XS2, sizeof(double) * 4 * np * np);
+    patch_free(&pd);
+    return r;
+}
+
+/* Edge root for tests: returns converged flag; t0 as (re, im). */
+int orc_edge_root(void *h, int P, int e, const double *yt, double *t0) {
+    orc_surface *S = h;
+    orc_patch pd;
+    setup_patch_of(S, P, &pd);
+    cplx t;
+    int c = edge_root(pd.ea + e * pd.p * 3, pd.p, yt, 30, &t);
+    t0[0] = creal(t); t0[1] = cimag(t);
+    patch_free(&pd);
+    return c;
+}
+
+/* Raw per-pair quantities for the Stokes-reduction pins: B^{lm} (4 reals per lm),
+ * Psi^{lm}, dB^{lm} and Omega = (Omega0, Omega_vec), dOmega; target in global
+ * coordinates.  Returns flags. */
+int orc_pair_B(void *h, int P, const double *xt, const double *nt, int self_i,
+               double *Bout, double *Psiout, double *dBout, double *Omout, double *dOmout) {
+    orc_surface *S = h;
+    orc_patch pd;
+    if (setup_patch_of(S, P, &pd)) { patch_free(&pd); return -1; }
+    orc_forms F;
+    int fl = pair_forms(&S->ord[pd.p], &pd, &S->opt, xt, nt, self_i, 1, &F);
+    for (int lm = 0; lm < pd.np; lm++) {
+        for (int c = 0; c < 4; c++) { Bout[4 * lm + c] = F.B[lm][c]; dBout[4 * lm + c] = F.Bd[lm][c]; }
+        Psiout[lm] = F.Psi[lm];
+    }
+    for (int c = 0; c < 4; c++) { Omout[c] = F.Om[c]; dOmout[c] = F.dOm[c]; }
+    patch_free(&pd);
+    return fl;
+}
