@@ -22,7 +22,11 @@ INV4PI = 1.0 / (4.0 * np.pi)
 
 def kernel(kind: str, tgt, tnrm, r, nrm):
     """K(r', r) for kind in S, D, SP, DP at source points r (..., 3) with normals nrm."""
-    d = tgt - r
+    return kernel_d(kind, tgt - r, tnrm, nrm)
+
+
+def kernel_d(kind: str, d, tnrm, nrm):
+    """The same kernels as functions of d = r' - r."""
     r2 = np.einsum("...a,...a->...", d, d)
     rr = np.sqrt(r2)
     if kind == "S":
@@ -98,7 +102,8 @@ def flat_triangle(kind: str, A, B, C, tgt, tnrm, mu, epsrel: float = 1e-13):
             rho, w = _radial_panels(abs(h), R)
             pts = p0[None, :] + rho[:, None] * dirv[None, :]
             uv = (pts - A[None, :]) @ Mp.T
-            k = kernel(kind, tgt, tnrm, pts, nu[None, :])
+            dvec = h * nu[None, :] - rho[:, None] * dirv[None, :]   # r' - r without cancellation
+            k = kernel_d(kind, dvec, tnrm, nu[None, :])
             return float(np.sum(w * rho * k * mu(uv[:, 0], uv[:, 1])))
 
         # the line P1P2 is closest to p0 at angle th_n: split there for smoothness
@@ -129,6 +134,7 @@ def _tri_rule(n: int):
 
 def curved_patch(integrand, X, tgt, size_ratio: float = 3.0, n: int = 14, max_depth: int = 14):
     """int over T of integrand(uv, X(uv), Xu x Xv) du dv by recursive subdivision.
+    The integrand may return (m,) or (m, ...) values for the m points.
 
     X(uv) -> (points (m,3), cross (m,3)) where cross = X_u x X_v (area element and
     normal).  A piece is accepted when its diameter * size_ratio < distance to tgt."""
@@ -149,5 +155,6 @@ def curved_patch(integrand, X, tgt, size_ratio: float = 3.0, n: int = 14, max_de
         jac = abs((b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1]))
         uv = a[None, :] + uvq[:, 0:1] * (b - a)[None, :] + uvq[:, 1:2] * (c - a)[None, :]
         pts, cr = X(uv)
-        total += jac * np.sum(wq * integrand(uv, pts, cr))
+        vals = np.asarray(integrand(uv, pts, cr))
+        total = total + jac * np.tensordot(wq, vals, axes=(0, 0))
     return total

@@ -245,3 +245,13 @@ def lu_solve(A, B):
     if r:
         raise np.linalg.LinAlgError("singular")
     return B
+
+
+def basis_batch(p: int, y):
+    """H^{(l,m)} and grad H^{(l,m)} (1 <= m <= l <= p) at points y (n, 3)."""
+    y = np.ascontiguousarray(y, np.float64).reshape(-1, 3)
+    npn = p * (p + 1) // 2
+    H = np.zeros((len(y), npn))
+    gH = np.zeros((len(y), npn, 3))
+    lib().orc_basis_batch(C.c_int(p), C.c_int64(len(y)), _p(y), _p(H), _p(gH))
+    return H, gH

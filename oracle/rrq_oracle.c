@@ -1343,3 +1343,23 @@ int orc_pair_B(void *h, int P, const double *xt, const double *nt, int self_i,
     patch_free(&pd);
     return fl;
 }
+
+/* H^{(l,m)} = sqrt2 Im S^{(l,m)} and grad H for 1 <= m <= l <= p at npts points
+ * (basis order lm = l(l-1)/2 + m - 1): H[npts][np], gH[npts][np][3]. */
+int orc_basis_batch(int p, int64_t npts, const double *y, double *H, double *gH) {
+    lowdeg_init();
+    int np = p * (p + 1) / 2;
+    for (int64_t n = 0; n < npts; n++) {
+        cplx S[NHFULL(ORC_LMAX)];
+        solid_S(p, y + 3 * n, S);
+        int lm = 0;
+        for (int l = 1; l <= p; l++)
+            for (int m = 1; m <= l; m++, lm++) {
+                cplx g[3];
+                grad_S(S, p, l, m, g);
+                H[n * np + lm] = sqrt(2.0) * cimag(S[HIDX(l, m)]);
+                for (int a = 0; a < 3; a++) gH[(n * np + lm) * 3 + a] = sqrt(2.0) * cimag(g[a]);
+            }
+    }
+    return 0;
+}

@@ -1,0 +1,153 @@
+"""Pins of the oracle's harmonic polynomials and 1-D quadrature pieces.
+
+Each check compares against mathematics that does not come from the oracle's own
+formulas: the addition theorem evaluated at independent points, the spherical
+harmonic addition identity, finite differences, Laplace's equation, the flat
+triangle theorem, textbook moments and scipy adaptive quadrature.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+
+def test_addition_theorem(oracle_lib):
+    """R_l^m(a+b) = sum_{j,k} R_j^k(a) R_{l-j}^{m-k}(b) T_{jk,lm} (Sec. 2.3, eqs.
+    l2ltranslation, tjklmdef) for random a, b: pins the Legendre recurrence, the
+    normalisation of R_l^m and the negative-m convention together."""
+    O = oracle_lib
+    rng = np.random.default_rng(7)
+    L = 10
+    for _ in range(3):
+        a = rng.standard_normal(3) * 0.6
+        b = rng.standard_normal(3) * 0.6
+        Ra, Rb, Rab = O.solid_R(L, a), O.solid_R(L, b), O.solid_R(L, a + b)
+        for l in range(L + 1):
+            for m in range(-l, l + 1):
+                s = 0
+                for j in range(l + 1):
+                    for k in range(-j, j + 1):
+                        if abs(m - k) > l - j:
+                            continue
+                        s += Ra[O.hidx(j, k)] * Rb[O.hidx(l - j, m - k)] * O.T(j, k, l, m)
+                assert abs(s - Rab[O.hidx(l, m)]) < 1e-13 * (1 + abs(Rab[O.hidx(l, m)]))
+
+
+def test_spherical_addition_identity(oracle_lib):
+    """sum_m |Y_l^m|^2 = 2l+1 with the paper's normalisation (no 1/sqrt(4 pi)),
+    i.e. sum_m |R_l^m(x)|^2 = |x|^{2l}."""
+    O = oracle_lib
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal(3)
+    R = O.solid_R(9, x)
+    r2 = x @ x
+    for l in range(10):
+        s = sum(abs(R[O.hidx(l, m)]) ** 2 for m in range(-l, l + 1))
+        assert abs(s - r2 ** l) < 1e-13 * r2 ** l
+
+
+def test_low_degree_closed_forms(oracle_lib):
+    """R_0^0 = 1, R_1^0 = z, |R_1^1| = rho/sqrt2, R_2^0 = (2z^2 - x^2 - y^2)/2."""
+    O = oracle_lib
+    x = np.array([0.3, -0.7, 0.45])
+    R = O.solid_R(2, x)
+    assert abs(R[O.hidx(0, 0)] - 1) < 1e-15
+    assert abs(R[O.hidx(1, 0)] - x[2]) < 1e-15
+    assert abs(abs(R[O.hidx(1, 1)]) - math.hypot(x[0], x[1]) / math.sqrt(2)) < 1e-15
+    assert abs(R[O.hidx(2, 0)] - (2 * x[2] ** 2 - x[0] ** 2 - x[1] ** 2) / 2) < 1e-15
+    # S(x,y,z) = R(y,z,x): the polar axis of S is the x axis
+    S = O.solid_S(2, x)
+    assert abs(S[O.hidx(1, 0)] - x[0]) < 1e-15
+
+
+@pytest.mark.parametrize("lm", [(2, 1), (4, -3), (7, 7), (8, 0), (6, 2)])
+def test_gradient_hessian_finite_difference(oracle_lib, lm):
+    O = oracle_lib
+    l, m = lm
+    y = np.array([0.21, -0.33, 0.17])
+    g, H = O.grad_hess_S(8, y, l, m)
+    h = 1e-4
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        fd = (-O.solid_S(8, y + 2 * e) + 8 * O.solid_S(8, y + e) - 8 * O.solid_S(8, y - e)
+              + O.solid_S(8, y - 2 * e)) / (12 * h)
+        assert abs(fd[O.hidx(l, m)] - g[a]) < 1e-10
+        g1, _ = O.grad_hess_S(8, y + e, l, m)
+        g2, _ = O.grad_hess_S(8, y - e, l, m)
+        assert np.abs((g1 - g2) / (2 * h) - H[:, a]).max() < 1e-7
+    # harmonic: Laplacian from second differences of the values
+    lap = 0
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = 1e-3
+        lap += (O.solid_S(8, y + e) - 2 * O.solid_S(8, y) + O.solid_S(8, y - e))[O.hidx(l, m)] / 1e-6
+    assert abs(lap) < 1e-5
+
+
+@pytest.mark.parametrize("p", [2, 4, 6, 8])
+def test_flat_triangle_basis_theorem(oracle_lib, p):
+    """Thm. trianglebasis: on z = 0, H^{(l,m)} = sqrt2 Im S^{(l,m)} vanishes, grad H is
+    along e_z, and F^{(l,m)} = dH/dz span all polynomials of degree <= p-1."""
+    O = oracle_lib
+    rng = np.random.default_rng(p)
+    pts = rng.random((3 * p * p, 2)) - 0.5
+    F = []
+    for (x, y) in pts:
+        S = O.solid_S(p, [x, y, 0.0])
+        row = []
+        for l in range(1, p + 1):
+            for m in range(1, l + 1):
+                assert abs(math.sqrt(2) * S[O.hidx(l, m)].imag) < 1e-15
+                g, _ = O.grad_hess_S(p, [x, y, 0.0], l, m)
+                Hg = math.sqrt(2) * g.imag
+                assert abs(Hg[0]) < 1e-14 and abs(Hg[1]) < 1e-14
+                row.append(Hg[2])
+        F.append(row)
+    F = np.array(F)
+    mono = np.array([[x ** a * y ** b for a in range(p) for b in range(p - a)] for (x, y) in pts])
+    # span equality: ranks of F, mono and [F mono] are all n_p
+    npn = p * (p + 1) // 2
+    assert np.linalg.matrix_rank(F, tol=1e-10) == npn
+    assert np.linalg.matrix_rank(np.hstack([F, mono]), tol=1e-9) == npn
+
+
+def test_gauss_legendre_exactness(oracle_lib):
+    O = oracle_lib
+    for n in (4, 8, 16, 32):
+        x, w = O.gauss_legendre(n)
+        for k in range(2 * n):
+            exact = 0.0 if k % 2 else 2.0 / (k + 1)
+            assert abs(np.sum(w * x ** k) - exact) < 1e-14
+
+
+@pytest.mark.parametrize("ab", [(0.3, 0.05), (-0.9, 1e-4), (1.2, 0.02), (0.0, 0.7), (0.5, 1e-7)])
+def test_ssq_moments_against_adaptive_quadrature(oracle_lib, ab):
+    """I_i = int t^i / ((t-a)^2+b^2)^{m/2} dt (Sec. 2.4, eq. ssq1dintegrals) for m = 1, 3."""
+    O = oracle_lib
+    a, b = ab
+    J, K = O.ssq_moments(16, a, b)
+    # reference by the substitution t - a = b sinh(s), which removes the near singularity
+    lo, hi = math.asinh((-1 - a) / b), math.asinh((1 - a) / b)
+    for i in range(16):
+        rj = quad(lambda s: (a + b * math.sinh(s)) ** i, lo, hi, limit=500, epsabs=0, epsrel=1e-13)[0]
+        rk = quad(lambda s: (a + b * math.sinh(s)) ** i / (b * math.cosh(s)) ** 2, lo, hi, limit=500,
+                  epsabs=0, epsrel=1e-13)[0]
+        assert abs(J[i] - rj) < 1e-12 * max(1.0, abs(J[0]))
+        assert abs(K[i] - rk) < 1e-11 * max(1.0, abs(K[0]))
+
+
+def test_bernstein_radius(oracle_lib):
+    O = oracle_lib
+    assert abs(O.bernstein_rho(0.3 + 0j) - 1.0) < 1e-14
+    assert abs(O.bernstein_rho(2.0 + 0j) - (2 + math.sqrt(3))) < 1e-13
+    assert abs(O.bernstein_rho(1j) - (1 + math.sqrt(2))) < 1e-13
+
+
+def test_lu_solve(oracle_lib):
+    O = oracle_lib
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((40, 40))
+    B = rng.standard_normal((40, 3))
+    assert np.abs(O.lu_solve(A, B) - np.linalg.solve(A, B)).max() < 1e-12
