@@ -1,0 +1,169 @@
+/*
+ * rrq.h -- C ABI of librrq: near-field quadrature corrections for the Laplace
+ * single/double layer potentials and their normal derivatives (S, D, S', D') on
+ * triangulated surfaces in 3D, by recursive reduction quadrature (Jiang & Zhu,
+ * arXiv 2411.08342), computed on one NVIDIA GB300 (sm_103a).
+ *
+ * What is computed.  For a target r' and a source patch P the correction row is
+ *     row_K(r', P)[i] = RRQ_K(r', P)[i] - K(r', x_i) w_i      (i = 0 .. n_p-1)
+ * where RRQ_K(r', P) is the row vector that maps the density values at the n_p
+ * nodes x_i of P to the integral over P of the kernel K against the harmonic fit of
+ * the density (Sec. 3, Thms. 3.2-3.5; Sec. 4 Steps 1-8 and the matrix-build remark),
+ * and K(r', x_i) w_i is the smooth-rule weight (omitted for the node that coincides
+ * with the target).  The kernels are (Sec. 1, eqs. slpdef-dprimelpdef):
+ *     S : G = 1/(4 pi |r'-r|)          D : dG/dnu (source normal)
+ *     S': dG/dnu' (target normal)      D': d^2 G / dnu' dnu
+ * On-surface targets that are nodes of P get the principal value for D and S'
+ * (the line integrals give the exterior limit; the jump 1/2 is applied), S and D'
+ * are continuous.  The correction matrix has one row per target and is stored as
+ * CSR; the columns of a row are the nodes of its near patches in ascending patch
+ * id, each patch's nodes in node order.  Near patches of a target t are those with
+ * |x_t - c_P| <= R_P + eta d_P (c_P: vertex mean, R_P: largest distance from c_P to
+ * the nodes and vertices, d_P: longest vertex-to-vertex edge), plus the patch that
+ * contains t as a node (Sec. 4, remark on near-target identification).
+ *
+ * Geometry.  Patch P of order p (2 <= p <= RRQ_PMAX) has n_p = p(p+1)/2 nodes: the
+ * images of the reference nodes ref_uv[p] (points (u,v) strictly inside the triangle
+ * (0,0),(1,0),(0,1), unisolvent for total degree p-1).  The patch surface is the
+ * degree p-1 interpolant of its node positions; its boundary is the image of the
+ * triangle's edges, oriented counter-clockwise about the outward normal.
+ *
+ * Conventions for every function:
+ *   - return RRQ_OK (0) on success, a negative rrq_status on error; no function
+ *     aborts the process; rrq_status_string() names a status;
+ *   - pointers are borrowed for the duration of the call only;
+ *   - input arrays are device pointers unless rrq_options.inputs_on_host = 1;
+ *   - all work is enqueued on the context's CUDA stream; functions that return
+ *     sizes or diagnostics synchronise that stream first;
+ *   - there is no CPU fallback: without a usable sm_103a device every entry point
+ *     that computes returns RRQ_ERR_CUDA.
+ */
+#ifndef RRQ_H
+#define RRQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RRQ_PMAX 8
+
+typedef int32_t rrq_status;
+enum {
+    RRQ_OK = 0,
+    RRQ_ERR_ARG = -1,          /* NULL pointer, size or order out of range, NaN input */
+    RRQ_ERR_CUDA = -2,         /* a CUDA call failed (message in rrq_last_error) */
+    RRQ_ERR_OOM = -3,          /* device allocation failed */
+    RRQ_ERR_DEGENERATE = -4,   /* a patch is degenerate or its fit matrix is singular */
+    RRQ_ERR_UNSUPPORTED = -5,  /* option combination not implemented (e.g. ptilde != 2p) */
+    RRQ_WARN_ROOTFIND = 1      /* success, but some pairs used the fallback edge rule */
+};
+
+/* Kernel selection bits (rrq_build_corrections kernel_mask; rrq_apply kernel). */
+enum { RRQ_S = 1, RRQ_D = 2, RRQ_SP = 4, RRQ_DP = 8 };
+
+typedef struct rrq_ctx rrq_ctx;
+
+/* One surface.  All arrays are read only. */
+typedef struct {
+    int32_t npatch;                 /* number of patches, >= 1 */
+    const int32_t *order;           /* [npatch] order p of each patch */
+    const int64_t *node_off;        /* [npatch+1] first node of each patch; node_off[0] = 0,
+                                       node_off[P+1] - node_off[P] = n_p(order[P]) */
+    const double *xyz;              /* [nnode][3] node positions */
+    const double *nrm;              /* [nnode][3] unit outward normals at the nodes */
+    const double *wts;              /* [nnode] smooth-rule weights (reference weight x area element) */
+    const double *ref_uv[RRQ_PMAX + 1]; /* ref_uv[p]: [n_p][2] reference nodes of order p
+                                       (host memory always); NULL for unused orders */
+} rrq_surface;
+
+/* Targets.  self_node[t] = global node id if target t is a surface node, else -1. */
+typedef struct {
+    int64_t ntarg;                  /* >= 0 */
+    const double *xyz;              /* [ntarg][3] */
+    const double *nrm;              /* [ntarg][3] unit normal nu' at the target (used by S', D') */
+    const int64_t *self_node;       /* [ntarg], or NULL = no target is a node */
+} rrq_targets;
+
+typedef struct {
+    int32_t inputs_on_host;  /* 1: surface/target arrays are host pointers (copied in) */
+    int32_t ptilde;          /* Gauss-Legendre nodes per edge; 0 = 2p (only 2p is implemented) */
+    double rho0;             /* singularity-swap used when the Bernstein radius of the
+                                complex preimage t0 is below rho0; 0 = 10^(5/ptilde) */
+    int32_t newton_max;      /* Newton iterations for t0; 0 = 30 */
+    double eta;              /* near factor; 0 = 1 */
+} rrq_options;
+
+/* CSR correction matrix in device memory owned by the library (rrq_csr_free). */
+typedef struct {
+    int64_t nrows;           /* = ntarg */
+    int64_t nnz;             /* entries per kernel */
+    int64_t npairs;          /* near (target, patch) pairs */
+    uint32_t kernel_mask;    /* kernels whose val[] is filled */
+    int64_t *rowptr;         /* [nrows+1] device */
+    int32_t *col;            /* [nnz] device, global node ids */
+    double *val[4];          /* [nnz] device each, for S, D, S', D' (NULL if not built) */
+} rrq_csr;
+
+/* Counters of the last build (pairs per category). */
+typedef struct {
+    int64_t npairs;
+    int64_t newton_fail;     /* an edge root did not converge: upsampled edge rule used */
+    int64_t on_edge;         /* target numerically on a patch edge: row unreliable */
+    int64_t u_poor;          /* no unit vector u kept min u.(r'-r)/|r'-r| above -1/2 */
+    int64_t ssq_edges;       /* edges evaluated by singularity swap */
+    int64_t far_edges;       /* edges evaluated by the upsampled Gauss rule */
+    double ms_near, ms_precompute, ms_pairs;  /* stage times of the last build (ms) */
+} rrq_diag;
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+rrq_status rrq_ctx_create(rrq_ctx **ctx, int device, void *cuda_stream);
+void rrq_ctx_destroy(rrq_ctx *ctx);
+
+/* Build the correction matrices for the kernels in kernel_mask (RRQ_S|RRQ_D|...)
+ * (Sec. 4 Steps 1-8 with the matrix-build remark; Sec. 3.6 for S', 3.7 for D';
+ * Sec. 5 eq. dlpsplitting for the correction = RRQ - smooth).  On success *out holds
+ * device buffers allocated by the library; free them with rrq_csr_free.  Synchronises
+ * the context stream.  Errors: RRQ_ERR_ARG for invalid sizes/orders/pointers,
+ * RRQ_ERR_DEGENERATE if a patch has zero area or a singular fit, RRQ_ERR_OOM,
+ * RRQ_ERR_CUDA; RRQ_WARN_ROOTFIND (> 0) when some pairs used the fallback rule. */
+rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
+                                 uint32_t kernel_mask, const rrq_options *opt, rrq_csr *out);
+
+/* Copy a CSR (built by rrq_build_corrections) into caller buffers: rowptr [nrows+1],
+ * col [nnz], val[k] [nnz] for each built kernel k (NULL entries are skipped).
+ * dst_on_host = 1 for host buffers (pinned or pageable), 0 for device buffers.
+ * Synchronises the context stream. */
+rrq_status rrq_csr_copy(rrq_ctx *ctx, const rrq_csr *csr, int64_t *rowptr, int32_t *col,
+                        double *val[4], int32_t dst_on_host);
+
+/* Free the device buffers of a CSR built by this context and zero the struct. */
+rrq_status rrq_csr_free(rrq_ctx *ctx, rrq_csr *csr);
+
+/* Apply one corrected operator (Sec. 5, eq. dlpsplitting):
+ *   out[t] = sum_{j : x_j != target t} K(x_t, x_j) w_j density[j] + sum_j C[t][j] density[j]
+ * with K the kernel `kernel` (one of RRQ_S, RRQ_D, RRQ_SP, RRQ_DP) and C its correction
+ * CSR.  density [nnode] and out [ntarg] follow inputs_on_host.  The smooth sum is a
+ * direct O(ntarg * nnode) sum (no fast multipole method). */
+rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, int32_t kernel,
+                     const rrq_csr *corr, const double *density, double *out, const rrq_options *opt);
+
+/* Counters and stage timings of the last rrq_build_corrections on this context. */
+rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag);
+
+/* Measured fused-multiply-add throughput of this device in TFLOP/s (2 flops per FMA),
+ * FP64 (fp32 = 0) or FP32 (fp32 = 1): 8 independent dependency chains per thread,
+ * 8 blocks of 256 threads per SM, timed with CUDA events.  Used as the roofline
+ * denominator of the ALU-bound correction build.  Synchronises the context stream. */
+rrq_status rrq_measure_fma_peak(rrq_ctx *ctx, int32_t fp32, double *tflops);
+
+/* Human-readable name of a status; message of the last CUDA error on this thread. */
+const char *rrq_status_string(rrq_status s);
+const char *rrq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,112 @@
+// Internal definitions shared by the librrq CUDA translation units.
+//
+// Harmonic normalisation used on the device.  The paper's regular solid harmonics
+// R_l^m (eq. rlmdef) are rescaled to Rn_l^m = R_l^m / sqrt((l-m)!(l+m)!), which turns
+// the translation coefficients T_{jk,lm} of eq. (tjklmdef) into 1:
+//     Rn_l^m(a + b) = sum_{j,k} Rn_j^k(a) Rn_{l-j}^{m-k}(b),
+// and gives ladder rules for derivatives (the j = 1 terms of that expansion):
+//     d/dZ Rn_l^m = Rn_{l-1}^m,  d/dX Rn_l^m = (Rn_{l-1}^{m-1} - Rn_{l-1}^{m+1})/2,
+//     d/dY Rn_l^m = i (Rn_{l-1}^{m-1} + Rn_{l-1}^{m+1})/2,
+// with Rn_l^{-m} = (-1)^m conj(Rn_l^m).  The basis S^{(l,m)}(x,y,z) = Rn_l^m(y,z,x)
+// (eq. slmdef) and H^{(l,m)} = sqrt2 Im S^{(l,m)} (eq. hlmslmconnection) then differ
+// from the paper's by a constant factor per (l,m), which leaves every correction row
+// unchanged: the rows depend only on the span of the basis.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rrq.h"
+
+#define RRQ_PTMAX (2 * RRQ_PMAX)
+#define RRQ_NPMAX (RRQ_PMAX * (RRQ_PMAX + 1) / 2)
+#define RRQ_NJKMAX ((RRQ_PMAX + 1) * (RRQ_PMAX + 2) / 2)
+#define RRQ_NOM 16
+
+struct cd {
+    double x, y;
+};
+
+__host__ __device__ __forceinline__ cd mkc(double a, double b) { cd r; r.x = a; r.y = b; return r; }
+__host__ __device__ __forceinline__ cd cadd(cd a, cd b) { return mkc(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cd csub(cd a, cd b) { return mkc(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cd cmul(cd a, cd b) { return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ __forceinline__ cd cscale(cd a, double s) { return mkc(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ cd cconj(cd a) { return mkc(a.x, -a.y); }
+__host__ __device__ __forceinline__ cd cmuli(cd a) { return mkc(-a.y, a.x); }  // i * a
+__host__ __device__ __forceinline__ double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ cd cdivz(cd a, cd b) {
+    double d = b.x * b.x + b.y * b.y;
+    return mkc((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// index of (n, q), 0 <= q <= n, in a triangular harmonic table
+__host__ __device__ __forceinline__ int jk_index(int n, int q) { return n * (n + 1) / 2 + q; }
+
+// Per-order constant tables (computed on the host by rrq_tables.cu).
+struct OrderTables {
+    int p, np, pt, nup, njk;
+    double rho0;
+    double tq[RRQ_PTMAX], wq[RRQ_PTMAX];            // edge Gauss-Legendre nodes/weights
+    double U[RRQ_PTMAX * RRQ_PTMAX];                // [i][q]: monomial coefficients c_i = sum_q U[i][q] F_q
+    double tu[2 * RRQ_PTMAX], wu[2 * RRQ_PTMAX];    // upsampled Gauss-Legendre rule
+    double Lup[2 * RRQ_PTMAX * RRQ_PTMAX];          // [s][q] Lagrange basis of tq at tu[s]
+    double tom[RRQ_NOM], wom[RRQ_NOM];              // Gauss-Legendre rule per Omega_0 panel
+    double Eint[(3 * RRQ_PTMAX + 3) * RRQ_NPMAX];   // [row][i]: node -> edge samples, then vertices
+    double LegW[RRQ_PMAX * RRQ_PTMAX];              // [n][q] (2n+1)/2 w_q P_n(t_q)
+    double dLeg[RRQ_PTMAX * RRQ_PMAX];              // [q][n] P_n'(t_q)
+    double LegU[2 * RRQ_PTMAX * RRQ_PMAX];          // [s][n] P_n(tu_s)
+};
+
+// Device-side per-patch data (strides sized for the largest order of the surface).
+struct PatchData {
+    int npatch;
+    int pmax;
+    double *frame;   // [P][16]  c[3], R[3][3] (R[a][b] = b-th frame vector, component a), s
+    double *bounds;  // [P][5]   c_P[3], R_P, d_P (global coordinates, for the near list)
+    double *ynode;   // [P][NPMAX*3] local node coordinates
+    double *ea;      // [P][3*PMAX*3] local Legendre coefficients of the 3 edges, [e][n][a]
+    double *ey;      // [P][3*PTMAX*3] local edge samples at the Gauss nodes, [e*pt+q][a]
+    double *et;      // [P][3*PTMAX*3] tangents dy/dt at the edge samples
+    double *eyu;     // [P][3*2PTMAX*3] local edge samples at the upsampled nodes
+    cd *eg;          // [P][3*PTMAX][NJKMAX][3] grad S^{(j,k)} at edge samples
+    cd *eh;          // [P][3*PTMAX][NJKMAX][3] (Hess S^{(j,k)}) tau at edge samples
+    double *XD;      // [P][4*NPMAX][NPMAX] quaternion fit of (mu, 0):    row c*np+lm, col i
+    double *XSp;     // [P][4*NPMAX][NPMAX] quaternion fit of (0, sigma nu)
+    double *XS2;     // [P][4*NPMAX][NPMAX] quaternion fit of the intermediate density
+    double *XS1;     // [P][NPMAX][NPMAX]   scalar fit A_S^{-1}
+    int *status;     // [P] 0 ok, nonzero = singular fit / degenerate patch
+};
+
+static const size_t PD_FRAME = 16, PD_BOUNDS = 5;
+__host__ __device__ __forceinline__ size_t pd_ynode() { return (size_t)RRQ_NPMAX * 3; }
+__host__ __device__ __forceinline__ size_t pd_ea() { return (size_t)3 * RRQ_PMAX * 3; }
+__host__ __device__ __forceinline__ size_t pd_ey() { return (size_t)3 * RRQ_PTMAX * 3; }
+__host__ __device__ __forceinline__ size_t pd_eyu() { return (size_t)3 * 2 * RRQ_PTMAX * 3; }
+__host__ __device__ __forceinline__ size_t pd_eg() { return (size_t)3 * RRQ_PTMAX * RRQ_NJKMAX * 3; }
+__host__ __device__ __forceinline__ size_t pd_X() { return (size_t)4 * RRQ_NPMAX * RRQ_NPMAX; }
+__host__ __device__ __forceinline__ size_t pd_XS1() { return (size_t)RRQ_NPMAX * RRQ_NPMAX; }
+
+// Pair work item: target, patch, offset of the first CSR entry of the pair.
+struct PairItem {
+    int64_t t;
+    int64_t off;
+    int32_t P;
+    int32_t pad;
+};
+
+// Device counters of a build.
+struct BuildCounters {
+    unsigned long long newton_fail, on_edge, u_poor, ssq_edges, far_edges;
+};
+
+// Host entry points implemented in the individual translation units.
+int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, OrderTables *out);
+cudaError_t rrq_launch_precompute(int p, const OrderTables *d_tab, const int32_t *d_plist, int n,
+                                  const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
+                                  PatchData pd, cudaStream_t st);
+cudaError_t rrq_launch_pairs(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems,
+                             PatchData pd, const int64_t *d_node_off, const double *d_xyz,
+                             const double *d_nrm, const double *d_wts, const double *d_txyz,
+                             const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
+                             int newton_max, double *vS, double *vD, double *vSp, double *vDp,
+                             int32_t *col, BuildCounters *cnt, cudaStream_t st);

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of librrq (include/rrq.h).
+
+Argument marshalling only: every step of the correction build and of the apply runs
+in the CUDA library.  Device arrays are torch CUDA tensors; host arrays are numpy
+arrays (used with inputs_on_host=1).  There is no CPU fallback: loading fails loudly
+when the library cannot be built or loaded, and every compute call needs a GPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PMAX = 8
+S, D, SP, DP = 1, 2, 4, 8
+KERNEL_BITS = {"S": S, "D": D, "SP": SP, "DP": DP}
+KERNEL_SLOT = {"S": 0, "D": 1, "SP": 2, "DP": 3}
+_lock = threading.Lock()
+_lib = None
+
+
+class Surface(C.Structure):
+    _fields_ = [("npatch", C.c_int32), ("order", C.c_void_p), ("node_off", C.c_void_p), ("xyz", C.c_void_p),
+                ("nrm", C.c_void_p), ("wts", C.c_void_p), ("ref_uv", C.c_void_p * (PMAX + 1))]
+
+
+class TargetsS(C.Structure):
+    _fields_ = [("ntarg", C.c_int64), ("xyz", C.c_void_p), ("nrm", C.c_void_p), ("self_node", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("inputs_on_host", C.c_int32), ("ptilde", C.c_int32), ("rho0", C.c_double),
+                ("newton_max", C.c_int32), ("eta", C.c_double)]
+
+
+class CSR(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("nnz", C.c_int64), ("npairs", C.c_int64), ("kernel_mask", C.c_uint32),
+                ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p * 4)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("npairs", C.c_int64), ("newton_fail", C.c_int64), ("on_edge", C.c_int64), ("u_poor", C.c_int64),
+                ("ssq_edges", C.c_int64), ("far_edges", C.c_int64), ("ms_near", C.c_double),
+                ("ms_precompute", C.c_double), ("ms_pairs", C.c_double)]
+
+
+class RRQError(RuntimeError):
+    pass
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load librrq.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            if not os.path.exists(path):
+                raise RRQError(f"librrq not found at {path}")
+            L = C.CDLL(path)
+            L.rrq_status_string.restype = C.c_char_p
+            L.rrq_last_error.restype = C.c_char_p
+            L.rrq_ctx_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]
+            L.rrq_ctx_destroy.argtypes = [C.c_void_p]
+            L.rrq_build_corrections.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS), C.c_uint32,
+                                                C.POINTER(Options), C.POINTER(CSR)]
+            L.rrq_csr_copy.argtypes = [C.c_void_p, C.POINTER(CSR), C.c_void_p, C.c_void_p, C.c_void_p * 4, C.c_int32]
+            L.rrq_csr_free.argtypes = [C.c_void_p, C.POINTER(CSR)]
+            L.rrq_apply.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS), C.c_int32, C.POINTER(CSR),
+                                    C.c_void_p, C.c_void_p, C.POINTER(Options)]
+            L.rrq_last_diagnostics.argtypes = [C.c_void_p, C.POINTER(Diag)]
+            L.rrq_measure_fma_peak.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st < 0:
+        L = load(False)
+        raise RRQError(f"{what}: {L.rrq_status_string(st).decode()} ({L.rrq_last_error().decode()})")
+    return st
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Context:
+    """An rrq context bound to a CUDA device and stream (torch stream or raw handle)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RRQError("a CUDA device is required (no CPU fallback)")
+        self.L = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self.h = C.c_void_p()
+        _check(self.L.rrq_ctx_create(C.byref(self.h), device, C.c_void_p(handle)), "rrq_ctx_create")
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.rrq_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- marshalling
+    def surface(self, order, node_off, xyz, nrm, wts, ref_uv: dict) -> Surface:
+        s = Surface()
+        s.npatch = int(order.shape[0])
+        s.order, s.node_off, s.xyz, s.nrm, s.wts = (_ptr(a) for a in (order, node_off, xyz, nrm, wts))
+        keep = [order, node_off, xyz, nrm, wts]
+        for p, uv in ref_uv.items():
+            uv = np.ascontiguousarray(uv, dtype=np.float64)
+            keep.append(uv)
+            s.ref_uv[p] = uv.ctypes.data
+        s._keep = keep
+        return s
+
+    def targets(self, xyz, nrm, self_node=None) -> TargetsS:
+        t = TargetsS()
+        t.ntarg = int(xyz.shape[0])
+        t.xyz, t.nrm = _ptr(xyz), _ptr(nrm)
+        t.self_node = _ptr(self_node)
+        t._keep = [xyz, nrm, self_node]
+        return t
+
+    # ------------------------------------------------------------- entry points
+    def build_corrections(self, surf: Surface, targ: TargetsS, kernels=("S", "D", "SP", "DP"),
+                          inputs_on_host: bool = False, rho0: float = 0.0, eta: float = 0.0,
+                          newton_max: int = 0) -> CSR:
+        mask = 0
+        for k in kernels:
+            mask |= KERNEL_BITS[k]
+        opt = Options(int(inputs_on_host), 0, rho0, newton_max, eta)
+        out = CSR()
+        st = self.L.rrq_build_corrections(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt), C.byref(out))
+        _check(st, "rrq_build_corrections")
+        self.last_status = st
+        return out
+
+    def csr_free(self, csr: CSR):
+        _check(self.L.rrq_csr_free(self.h, C.byref(csr)), "rrq_csr_free")
+
+    def csr_to_torch(self, csr: CSR, kernels=("S", "D", "SP", "DP")):
+        """Copy a library CSR into torch CUDA tensors: (rowptr, col, {kernel: val})."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        rowptr = torch.empty(csr.nrows + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(max(csr.nnz, 1), dtype=torch.int32, device=dev)
+        vals = {k: torch.empty(max(csr.nnz, 1), dtype=torch.float64, device=dev) for k in kernels}
+        arr = (C.c_void_p * 4)()
+        for k, v in vals.items():
+            arr[KERNEL_SLOT[k]] = v.data_ptr()
+        _check(self.L.rrq_csr_copy(self.h, C.byref(csr), _ptr(rowptr), _ptr(col), arr, 0), "rrq_csr_copy")
+        return rowptr, col[: csr.nnz], {k: v[: csr.nnz] for k, v in vals.items()}
+
+    def csr_to_host(self, csr: CSR, kernels=("S", "D", "SP", "DP"), out=None):
+        """Copy a library CSR into (pinned or plain) numpy host buffers."""
+        if out is None:
+            out = (np.empty(csr.nrows + 1, np.int64), np.empty(max(csr.nnz, 1), np.int32),
+                   {k: np.empty(max(csr.nnz, 1), np.float64) for k in kernels})
+        rowptr, col, vals = out
+        arr = (C.c_void_p * 4)()
+        for k, v in vals.items():
+            arr[KERNEL_SLOT[k]] = v.ctypes.data
+        _check(self.L.rrq_csr_copy(self.h, C.byref(csr), _ptr(rowptr), _ptr(col), arr, 1), "rrq_csr_copy")
+        return rowptr, col, vals
+
+    def apply(self, surf: Surface, targ: TargetsS, kernel: str, csr: CSR, density, out,
+              inputs_on_host: bool = False):
+        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0)
+        _check(self.L.rrq_apply(self.h, C.byref(surf), C.byref(targ), KERNEL_BITS[kernel],
+                                C.byref(csr) if csr is not None else None, _ptr(density), _ptr(out),
+                                C.byref(opt)), "rrq_apply")
+        return out
+
+    def fma_peak_tflops(self, fp32: bool = False) -> float:
+        v = C.c_double()
+        _check(self.L.rrq_measure_fma_peak(self.h, int(fp32), C.byref(v)), "rrq_measure_fma_peak")
+        return v.value
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        _check(self.L.rrq_last_diagnostics(self.h, C.byref(d)), "rrq_last_diagnostics")
+        return {f: getattr(d, f) for f, _ in Diag._fields_}
+
+
+def device_inputs(disc, targets, device="cuda"):
+    """Torch CUDA copies of a workloads.Discretization and workloads.Targets."""
+    import torch
+    dev = torch.device(device)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev)
+    return dict(order=t(disc.order, torch.int32), node_off=t(disc.node_off, torch.int64),
+                xyz=t(disc.xyz, torch.float64), nrm=t(disc.nrm, torch.float64), wts=t(disc.wts, torch.float64),
+                txyz=t(targets.xyz, torch.float64), tnrm=t(targets.nrm, torch.float64),
+                tself=t(targets.self_node, torch.int64))

@@ -1,0 +1,168 @@
+"""CUDA path (through the C ABI) against the CPU FP64 oracle, element by element.
+
+CSR structure (row pointers, columns) must be identical; values must agree to
+E <= 1e-10 (see gpu_helpers.row_error).  Sizes span several tiles and ragged tails:
+orders 2..8, on-surface (self and near) and off-surface targets down to 1e-6 h.
+"""
+import numpy as np
+import pytest
+
+from paper_2411_08342_gb300 import workloads as W
+from tests.gpu_helpers import KINDS, TOL_E, gpu_build, row_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    c = rrq.Context(0)
+    yield c
+    c.close()
+
+
+def _compare(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_host=False):
+    rowptr, col, vals, diag = gpu_build(ctx, d, tg, kernels, on_host=on_host)
+    osf = oracle_lib.OracleSurface(d)
+    if tsel is None:
+        orp, ocol, ovals, _ = osf.csr_rows(tg, kernels=kernels)
+        grp, gcol, gvals = rowptr, col, vals
+        sub = tg
+    else:
+        tsel = np.asarray(tsel)
+        orp, ocol, ovals, _ = osf.csr_rows(tg, tsel, kernels=kernels)
+        lens = rowptr[tsel + 1] - rowptr[tsel]
+        grp = np.zeros(len(tsel) + 1, np.int64)
+        np.cumsum(lens, out=grp[1:])
+        idx = np.concatenate([np.arange(rowptr[t], rowptr[t + 1]) for t in tsel]) if len(tsel) else np.zeros(0, int)
+        gcol = col[idx]
+        gvals = {k: vals[k][idx] for k in kernels}
+        sub = W.Targets(tg.xyz[tsel], tg.nrm[tsel], tg.self_node[tsel])
+    assert np.array_equal(grp, orp), "row pointers differ"
+    assert np.array_equal(gcol, ocol), "columns differ"
+    errs = {k: row_error(k, d, sub, orp, ocol, gvals[k], ovals[k]) for k in kernels}
+    for k in kernels:
+        assert np.all(np.isfinite(gvals[k])), k
+        assert errs[k] <= TOL_E, errs
+    return errs, diag
+
+
+@pytest.mark.parametrize("p", [4, 5])
+def test_sphere80_all_rows(ctx, oracle_lib, p):
+    """Unit sphere, 80 patches, all on-surface nodes, S D S' D'."""
+    d, tg = W.sphere80(p)
+    errs, diag = _compare(ctx, oracle_lib, d, tg)
+    assert diag["on_edge"] == 0
+
+
+@pytest.mark.parametrize("p", [2, 3, 6, 7, 8])
+def test_orders_on_and_off_surface(ctx, oracle_lib, p):
+    d = W.discretize(W.star_surface(2), p)
+    rng = np.random.default_rng(p)
+    on = W.on_surface_targets(d)
+    sel = rng.choice(on.n, min(on.n, 300), replace=False)
+    tg = W.concat_targets(W.Targets(on.xyz[sel], on.nrm[sel], on.self_node[sel]),
+                          W.off_surface_targets(d, 300, seed=p))
+    _compare(ctx, oracle_lib, d, tg)
+
+
+def test_star1280_offsurface_p6(ctx, oracle_lib):
+    """The star surface (1280 patches, p = 6) with 3000 targets at 10^-k h, k ~ U[0,6]."""
+    d, tg = W.star1280(6, 3000)
+    _compare(ctx, oracle_lib, d, tg)
+
+
+def test_host_inputs_same_as_device(ctx, oracle_lib):
+    d, tg = W.sphere80(4)
+    a = gpu_build(ctx, d, tg, on_host=False)
+    b = gpu_build(ctx, d, tg, on_host=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for k in KINDS:
+        assert np.array_equal(a[2][k], b[2][k])
+
+
+def test_mixed_orders(ctx, oracle_lib):
+    """Patches of orders 3, 4, 6 in one surface."""
+    base = W.sphere_surface(2)
+    rng = np.random.default_rng(0)
+    orders = rng.choice([3, 4, 6], base.npatch)
+    parts = [W.discretize(base, p) for p in (3, 4, 6)]
+    xyz, nrm, wts, node_off = [], [], [], [0]
+    for P, p in enumerate(orders):
+        dp = parts[[3, 4, 6].index(p)]
+        a, b = dp.node_off[P], dp.node_off[P + 1]
+        xyz.append(dp.xyz[a:b]); nrm.append(dp.nrm[a:b]); wts.append(dp.wts[a:b])
+        node_off.append(node_off[-1] + b - a)
+    d = W.Discretization(p=6, npatch=base.npatch, order=orders.astype(np.int32),
+                         node_off=np.array(node_off, np.int64), xyz=np.concatenate(xyz), nrm=np.concatenate(nrm),
+                         wts=np.concatenate(wts), ref_uv={p: W.ref_nodes(p) for p in (3, 4, 6)}, surface=base)
+    on = W.on_surface_targets(d)
+    tg = W.concat_targets(on, W.Targets(on.xyz[::7] + 0.01 * on.nrm[::7], on.nrm[::7],
+                                        -np.ones(len(on.xyz[::7]), np.int64)))
+    _compare(ctx, oracle_lib, d, tg)
+
+
+def test_edge_cases(ctx, oracle_lib):
+    """No targets; targets far from the surface (empty rows); one patch, one target."""
+    d, tg = W.sphere80(4)
+    empty = W.Targets(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, np.int64))
+    rowptr, col, vals, diag = gpu_build(ctx, d, empty)
+    assert rowptr.tolist() == [0] and len(col) == 0
+    far = W.Targets(np.array([[10.0, 0, 0], [0, -7.0, 3.0]]), np.array([[1.0, 0, 0], [0, 1.0, 0]]),
+                    np.array([-1, -1], np.int64))
+    rowptr, col, vals, diag = gpu_build(ctx, d, far)
+    assert rowptr.tolist() == [0, 0, 0]
+    one = W.discretize(W.flat_surface(np.array([[[0, 0, 0], [1.0, 0, 0], [0, 1.0, 0]]])), 5)
+    t1 = W.Targets(np.array([[0.3, 0.3, 1e-5]]), np.array([[0, 0, 1.0]]), np.array([-1], np.int64))
+    _compare(ctx, oracle_lib, one, t1)
+
+
+def test_bad_arguments(ctx):
+    from paper_2411_08342_gb300 import rrq
+    d, tg = W.sphere80(4)
+    bad = d.order.copy()
+    bad[3] = 11
+    arrs = {k: np.ascontiguousarray(v) for k, v in dict(node_off=d.node_off, xyz=d.xyz, nrm=d.nrm, wts=d.wts).items()}
+    surf = ctx.surface(bad, arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
+    targ = ctx.targets(np.ascontiguousarray(tg.xyz), np.ascontiguousarray(tg.nrm), np.ascontiguousarray(tg.self_node))
+    with pytest.raises(rrq.RRQError, match="invalid argument"):
+        ctx.build_corrections(surf, targ, inputs_on_host=True)
+
+
+def test_full_size_sampled_rows(ctx, oracle_lib):
+    """The benchmark workload (star, 1280 patches, p = 6, 200k targets) built in full
+    on the GPU, with 200 seeded rows checked against the oracle."""
+    d, tg = W.star1280(6, 200_000)
+    rng = np.random.default_rng(11)
+    tsel = np.sort(rng.choice(tg.n, 200, replace=False))
+    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel)
+    assert diag["npairs"] > 200_000 * 10
+
+
+def test_apply_matches_reference(ctx, oracle_lib):
+    """rrq_apply = smooth direct sum + CSR . sigma, against numpy on the oracle's CSR."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    from oracle import brute
+    d, tg = W.sphere80(5)
+    sig = W.random_ylm_density(d.xyz, 4, seed=3)
+    arrs = rrq.device_inputs(d, tg)
+    surf = ctx.surface(arrs["order"], arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
+    targ = ctx.targets(arrs["txyz"], arrs["tnrm"], arrs["tself"])
+    csr = ctx.build_corrections(surf, targ)
+    osf = oracle_lib.OracleSurface(d)
+    orp, ocol, ovals, _ = osf.csr_rows(tg)
+    sdev = torch.as_tensor(sig, dtype=torch.float64, device="cuda")
+    for k in KINDS:
+        out = torch.empty(tg.n, dtype=torch.float64, device="cuda")
+        ctx.apply(surf, targ, k, csr, sdev, out)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            K = brute.kernel(k, tg.xyz[:, None], tg.nrm[:, None], d.xyz[None], d.nrm[None])
+        K[np.arange(tg.n), tg.self_node] = 0
+        ref = K @ (d.wts * sig) + np.add.reduceat(ovals[k] * sig[ocol], orp[:-1])
+        got = out.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), k
+    ctx.csr_free(csr)
