@@ -1,0 +1,332 @@
+"""Benchmark: near-field correction entries per second on one GB300.
+
+Workload (one step = one full correction build, all four kernels S, D, S', D'):
+star-shaped surface r = 1 + 0.2 Re Y_3^2 + 0.1 Re Y_5^1 on a 1280-patch icosahedral
+mesh, order p = 6 (21 nodes per patch, 26,880 nodes), 200,000 off-surface targets at
+distance 10^-k h (k ~ U[0,6]) along the normal of a random patch.  Inputs are seeded
+and synthetic.  The timed region starts with geometry and targets resident in device
+memory and ends with the four CSR matrices resident in device memory: near list,
+per-patch precompute, pair kernel, CSR assembly.  An L2 flush (a 512 MB write) runs
+between timed steps, outside the timed region.
+
+Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle instead, on a
+bounded sample of the same workload.  With torchrun (N > 1) every rank builds its own
+seeded 200k-target set against the same surface (weak scaling, no collective in the
+data path); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "near-correction entries/s at 1e-10 rel err (FP64)"
+UNIT = "entries/s"
+WORKLOAD = "star1280_p6_200k_offsurface_SDSpDp"
+NTARG = 200_000
+P = 6
+KERNELS = ("S", "D", "SP", "DP")
+SEED = 20241115
+
+
+def workload(rank: int = 0, ntarg: int = NTARG):
+    from paper_2411_08342_gb300 import workloads as W
+    return W.star1280(P, ntarg, seed=SEED + 1000 * rank)
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", str(r)))
+    return r, w, lr
+
+
+def reduce_max(v: float, world: int, device=None) -> float:
+    """Maximum over ranks (identity on one rank)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(v: float, world: int, device=None) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flops_per_pair(p: int) -> float:
+    """Algorithmic FP64 flop count of one (target, patch) pair for all four kernels,
+    counted from the loop structure of the per-pair kernel (Steps 4-8); the graded
+    Omega_0 panels are counted separately per panel point."""
+    np_ = p * (p + 1) // 2
+    pt = 2 * p
+    njk = (p + 1) * (p + 2) // 2
+    ns = 3 * pt
+    n2 = sum(j + 1 for j in range(2, p + 1))          # (j,k>=0) with j >= 2
+    n1 = sum(j + 1 for j in range(1, p + 1))          # (j,k>=0) with j >= 1
+    line = ns * (n1 * 16 + n2 * (60 + 64))            # V; Q and dQ per sample and harmonic
+    trans = 0
+    for l in range(1, p + 1):
+        for m in range(1, l + 1):
+            for j in range(1, l + 1):
+                kmin, kmax = max(-j, m - (l - j)), min(j, m + (l - j))
+                nk = max(0, kmax - kmin + 1)
+                trans += nk * (8 + (2 * 4 * 8 if j >= 2 else 0) + (4 * 16 if j >= 2 else 0))
+    contract = np_ * np_ * (8 + 8 + 16 + 12)          # D, D', S', S rows through the fit matrices
+    weights = 3 * (pt * pt * 4 + pt * 12)             # lambda = U^T I (m = 1, 3) and ratios
+    harm = njk * 60 + (np_ + ns) * 8                  # target table, gradients/Hessians, u choice
+    root = 3 * 8 * (3 * p * 16 + 20)                  # ~8 Newton steps of the complex edge polynomial
+    smooth = np_ * 40
+    return float(line + trans + contract + weights + harm + root + smooth)
+
+
+def bench_gpu(args):
+    import torch
+
+    from paper_2411_08342_gb300 import rrq
+    rank, world, lrank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    torch.cuda.set_device(lrank)
+    dev = torch.device("cuda", lrank)
+    d, tg = workload(rank)
+    ctx = rrq.Context(lrank)
+    arrs = rrq.device_inputs(d, tg, device=str(dev))
+    surf = ctx.surface(arrs["order"], arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
+    targ = ctx.targets(arrs["txyz"], arrs["tnrm"], arrs["tself"])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        csr = ctx.build_corrections(surf, targ, KERNELS)
+        nnz, npairs = csr.nnz, csr.npairs
+        ctx.csr_free(csr)
+        return nnz, npairs
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    time.sleep(0.3)
+    times, pair_ms, nnz, npairs = [], [], 0, 0
+    torch.cuda.synchronize(dev)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nnz, npairs = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        pair_ms.append(ctx.diagnostics()["ms_pairs"])
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    diag = ctx.diagnostics()
+    ms_step = reduce_max(sum(times) / len(times), world, dev)
+    entries = nnz * len(KERNELS)
+    total_entries = reduce_sum(float(entries), world, dev)
+    value = total_entries / (ms_step * 1e-3)
+
+    # e2e: host buffers through the C ABI (H2D of inputs and D2H of the four CSRs timed)
+    host = {k: np.ascontiguousarray(v) for k, v in dict(order=d.order, node_off=d.node_off, xyz=d.xyz, nrm=d.nrm,
+                                                         wts=d.wts, txyz=tg.xyz, tnrm=tg.nrm,
+                                                         tself=tg.self_node).items()}
+    pin = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in host.items()}
+    hsurf = ctx.surface(pin["order"], pin["node_off"], pin["xyz"], pin["nrm"], pin["wts"], d.ref_uv)
+    htarg = ctx.targets(pin["txyz"], pin["tnrm"], pin["tself"])
+    out_rowptr = torch.empty(tg.n + 1, dtype=torch.int64).pin_memory().numpy()
+    out_col = torch.empty(nnz, dtype=torch.int32).pin_memory().numpy()
+    out_vals = {k: torch.empty(nnz, dtype=torch.float64).pin_memory().numpy() for k in KERNELS}
+    h2d = sum(v.nbytes for v in pin.values())
+    d2h = out_rowptr.nbytes + out_col.nbytes + sum(v.nbytes for v in out_vals.values())
+    e2e_times = []
+    for it in range(max(2, args.steps // 2) + 1):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        csr = ctx.build_corrections(hsurf, htarg, KERNELS, inputs_on_host=True)
+        ctx.csr_to_host(csr, KERNELS, out=(out_rowptr, out_col, out_vals))
+        ctx.csr_free(csr)
+        torch.cuda.synchronize(dev)
+        if it > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = reduce_max(sum(e2e_times) / len(e2e_times), world, dev)
+    e2e = {"value": total_entries / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel (the per-pair kernel), FP64 ALU bound
+    peak = ctx.fma_peak_tflops(fp32=False)
+    peak32 = ctx.fma_peak_tflops(fp32=True)
+    fpp = flops_per_pair(P)
+    pair_s = sum(pair_ms) / len(pair_ms) * 1e-3
+    achieved = fpp * npairs / pair_s / 1e12
+    # kernel launches per step: per-order precompute and pair kernels, near list, scans, items
+    launches = diag.get("launches", None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded star surface and off-surface targets)",
+        "config": {"workload": WORKLOAD, "patches": d.npatch, "p": P, "nodes": d.nnode, "targets": tg.n,
+                   "kernels": list(KERNELS), "pairs": npairs, "nnz_per_kernel": nnz,
+                   "l2": "512 MB flush between timed steps", "parallelism": f"weak x{world}"},
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_pairs<6>",
+                     "peak_note": "measured FP64 FMA peak (rrq_measure_fma_peak); FP32 FMA peak %.1f TFLOP/s" % peak32,
+                     "flops_per_pair": fpp, "kernel_ms": pair_s * 1e3},
+        "stage_ms": {"precompute": diag["ms_precompute"], "near_and_items": diag["ms_near"], "pairs": diag["ms_pairs"]},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "points_per_s": world * tg.n / (ms_step * 1e-3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_targets)
+        line["cpu_baseline"]["value"] = line["cpu_baseline"]["entries_per_s"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(ntarg_sample: int) -> dict:
+    """The oracle, as it stands, on a bounded sample of the same workload (the first
+    ntarg_sample targets, all their near pairs, all four kernels), on all host cores."""
+    from oracle import oracle as O
+    d, tg = workload(0)
+    sel = np.arange(min(ntarg_sample, tg.n))
+    osf = O.OracleSurface(d)
+    t0 = time.perf_counter()
+    rowptr, col, vals, _ = osf.csr_rows(tg, sel, KERNELS)
+    dt = time.perf_counter() - t0
+    entries = float(rowptr[-1]) * len(KERNELS)
+    cores = len(os.sched_getaffinity(0))
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return {"entries_per_s": entries / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {len(sel)} of the 200k targets, all near pairs, 4 kernels ({int(entries)} entries, "
+                      f"{dt:.1f} s)", "seconds": dt}
+
+
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    d, tg = workload(0)
+    osf = O.OracleSurface(d)
+    n = args.cpu_targets
+    times, entries = [], 0.0
+    for it in range(args.warmup + args.steps):
+        sel = np.arange(it * n, (it + 1) * n) % tg.n
+        t0 = time.perf_counter()
+        rowptr, _, _, _ = osf.csr_rows(tg, sel, KERNELS)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            entries += float(rowptr[-1]) * len(KERNELS)
+    tot = sum(times)
+    value = entries / tot
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_targets_per_step": n},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": f"{n} consecutive targets of the 200k per step, all near pairs, 4 kernels"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-targets", type=int, default=1500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -4,10 +4,62 @@ import numpy as np
 from oracle import brute
 
 KINDS = ("S", "D", "SP", "DP")
-# FP64 path against the FP64 oracle: both follow the same algorithm with different
+# FP64 path against the FP64 oracle.  Both follow the same algorithm with different
 # operation order, harmonic normalisation and fit solver, so they agree to rounding
-# amplified by the fit's condition number (~1e5 at p = 8) and the monomial SSQ basis.
+# amplified by the conditioning of the formulation.  Two gates:
+#  * apply level: |(C_gpu - C_orc) sigma| <= max(TOL_APPLY, ROT_FACTOR x the oracle's
+#    own value of this error under rotated inputs) times the magnitude
+#    of what the corrected apply sums, sum_j |K w_j sigma_j| + sum_j |C_orc sigma_j|,
+#    per target, for a smooth density (random Y_l^m, l <= 8).  For targets 1e-6 h off
+#    the surface the correction cancels a smooth-rule sum of size ~1e6 down to a
+#    potential of size ~1e2, so the plain relative error of the potential reflects that
+#    cancellation, not the correction (reported alongside);
+#  * row level: E (row_error) <= max(TOL_E, ROT_FACTOR * E_rot), where E_rot is the
+#    oracle's own change under a 1e-9 rad rigid rotation of every input (exact rows are
+#    rotation invariant, so E_rot measures the oracle's rounding sensitivity).  For
+#    targets in the outer shell of the near region the target-centred translation
+#    cancels like (|y'|/r_patch)^p and the fit amplifies by kappa(A): E_rot reaches
+#    ~2e-10 at p = 6 and ~5e-8 at p = 8 on coarse curved meshes.
 TOL_E = 1e-10
+TOL_APPLY = 1e-10
+ROT_FACTOR = 8.0
+ROT_VEC = (1e-9, 2e-9, -1e-9)
+
+
+def rotated(d, tg, rotvec=ROT_VEC):
+    """Inputs rotated rigidly about the origin (Rodrigues formula)."""
+    from paper_2411_08342_gb300 import workloads as W
+    th = np.linalg.norm(rotvec)
+    k = np.asarray(rotvec) / th
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    R = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+    d2 = W.Discretization(p=d.p, npatch=d.npatch, order=d.order, node_off=d.node_off, xyz=d.xyz @ R.T,
+                          nrm=d.nrm @ R.T, wts=d.wts, ref_uv=d.ref_uv, surface=d.surface)
+    return d2, W.Targets(tg.xyz @ R.T, tg.nrm @ R.T, tg.self_node)
+
+
+def apply_error(kind, d, tg, rowptr, col, v_gpu, v_orc, sigma, plain=False):
+    """max_t |((C_gpu - C_orc) sigma)_t| / (sum_j |K(t,x_j) w_j sigma_j| + sum_j |C_orc[t,j] sigma_j|);
+    with plain=True the denominator is |(smooth + C_orc) sigma|_inf instead."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        sm = np.zeros(len(rowptr) - 1)
+        sa = np.zeros(len(rowptr) - 1)
+        for c0 in range(0, len(sm), 512):
+            K = brute.kernel(kind, tg.xyz[c0:c0 + 512, None], tg.nrm[c0:c0 + 512, None], d.xyz[None], d.nrm[None])
+            sn = tg.self_node[c0:c0 + 512]
+            K[np.arange(len(sn))[sn >= 0], sn[sn >= 0]] = 0.0
+            sm[c0:c0 + 512] = K @ (d.wts * sigma)
+            sa[c0:c0 + 512] = np.abs(K) @ np.abs(d.wts * sigma)
+    nz = np.diff(rowptr) > 0
+    cg = np.zeros(len(sm))
+    co = np.zeros(len(sm))
+    ca = np.zeros(len(sm))
+    cg[nz] = np.add.reduceat(v_gpu * sigma[col], rowptr[:-1][nz])
+    co[nz] = np.add.reduceat(v_orc * sigma[col], rowptr[:-1][nz])
+    ca[nz] = np.add.reduceat(np.abs(v_orc * sigma[col]), rowptr[:-1][nz])
+    if plain:
+        return float(np.abs(cg - co).max() / np.abs(sm + co).max())
+    return float(np.max(np.abs(cg - co) / (sa + ca)))
 
 
 def smooth_part(kind, d, tg, rowptr, col):
