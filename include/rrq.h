@@ -115,6 +115,7 @@ typedef struct {
     int64_t ssq_edges;       /* edges evaluated by singularity swap */
     int64_t far_edges;       /* edges evaluated by the upsampled Gauss rule */
     double ms_near, ms_precompute, ms_pairs;  /* stage times of the last build (ms) */
+    int64_t kernel_launches; /* CUDA kernels the last build launched */
 } rrq_diag;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream`

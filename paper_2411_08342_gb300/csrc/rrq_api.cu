@@ -266,6 +266,7 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     const int newton_max = o.newton_max > 0 ? o.newton_max : 30;
     CK(cudaSetDevice(ctx->device));
     memset(&ctx->diag, 0, sizeof(ctx->diag));
+    rrq_launch_counter() = 0;
     Scratch s;
     s.st = ctx->stream;
     Inputs in;
@@ -417,6 +418,7 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     ctx->diag.ms_near = ms;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     ctx->diag.ms_pairs = ms;
+    ctx->diag.kernel_launches = rrq_launch_counter();
     return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
 }
 

@@ -99,6 +99,11 @@ struct BuildCounters {
     unsigned long long newton_fail, on_edge, u_poor, ssq_edges, far_edges;
 };
 
+// Kernel launches issued by the library on this host thread since the last reset
+// (reported in rrq_diag.kernel_launches).
+int64_t &rrq_launch_counter();
+#define RRQ_COUNT_LAUNCH() (++rrq_launch_counter())
+
 // Host entry points implemented in the individual translation units.
 int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, OrderTables *out);
 cudaError_t rrq_launch_precompute(int p, const OrderTables *d_tab, const int32_t *d_plist, int n,

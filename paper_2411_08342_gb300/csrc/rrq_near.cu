@@ -16,6 +16,11 @@
 __global__ void rrq_widen_int(const int *in, int64_t *out, int64_t n);
 __global__ void rrq_narrow_int(const int64_t *in, int *out, int64_t n);
 
+int64_t &rrq_launch_counter() {
+    static thread_local int64_t n = 0;
+    return n;
+}
+
 static double bits_to_double(long long b) {
     double d;
     memcpy(&d, &b, sizeof(d));
@@ -218,12 +223,15 @@ cudaError_t rrq_scan_exclusive(const int64_t *in, int64_t *out, int64_t n, int64
     int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
     int64_t *bsum = tmp, *boff = tmp + nb + 1;
     k_scan_block<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, out, n, bsum);
+    RRQ_COUNT_LAUNCH();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (nb > 1) {
         e = rrq_scan_exclusive(bsum, boff, nb, tmp + 2 * nb + 2, st);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return e; {
         k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(out, n, boff);
+        RRQ_COUNT_LAUNCH();
+    }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         // total = boff[nb]
@@ -263,8 +271,10 @@ cudaError_t rrq_near_build(const double *d_bounds, int npatch, const int64_t *d_
     for (int a = 0; a < 3; a++) { init[1 + a] = ~0ULL; init[4 + a] = 0ULL; }
     init[7] = 0ULL;
     cudaError_t e = cudaMemcpyAsync(red, init, sizeof(init), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return e; {
     k_patch_reach<<<(npatch + 255) / 256, 256, 0, st>>>(d_bounds, npatch, eta, red);
+    RRQ_COUNT_LAUNCH();
+}
     unsigned long long hred[8];
     e = cudaMemcpyAsync(hred, red, sizeof(hred), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
@@ -300,26 +310,33 @@ cudaError_t rrq_near_build(const double *d_bounds, int npatch, const int64_t *d_
     if (!cell_cnt || !cell_items || !cell_tmp || !scan_tmp) return cudaErrorMemoryAllocation;
     cudaMemsetAsync(cell_cnt, 0, sizeof(int) * (ncell + 1), st);
     k_bin_count<<<(npatch + 255) / 256, 256, 0, st>>>(d_bounds, npatch, g, cell_cnt);
+    RRQ_COUNT_LAUNCH();
     // scan in int64 then narrow (ncell <= 2^24, npatch < 2^31)
     // widen counts
     {
         int64_t *wide = cell_tmp, *wscan = cell_tmp + (ncell + 1);
         rrq_widen_int<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(cell_cnt, wide, (int64_t)ncell);
+        RRQ_COUNT_LAUNCH();
         e = rrq_scan_exclusive(wide, wscan, (int64_t)ncell, scan_tmp, st);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return e; {
         rrq_narrow_int<<<(unsigned)((ncell + 1 + 255) / 256), 256, 0, st>>>(wscan, cell_cnt, (int64_t)ncell + 1);
+        RRQ_COUNT_LAUNCH();
+    }
     }
     int *cursor = (int *)alloc(actx, sizeof(int) * (ncell + 1));
     if (!cursor) return cudaErrorMemoryAllocation;
     cudaMemcpyAsync(cursor, cell_cnt, sizeof(int) * (ncell + 1), cudaMemcpyDeviceToDevice, st);
     k_bin_fill<<<(npatch + 255) / 256, 256, 0, st>>>(d_bounds, npatch, g, cursor, cell_items);
+    RRQ_COUNT_LAUNCH();
     int64_t *cnt = (int64_t *)alloc(actx, sizeof(int64_t) * (ntarg + 1));
     out->poff = (int64_t *)alloc(actx, sizeof(int64_t) * (ntarg + 1));
     if (!cnt || !out->poff) return cudaErrorMemoryAllocation;
     unsigned tb = (unsigned)((ntarg + 127) / 128);
-    if (ntarg > 0)
+    if (ntarg > 0) {
         k_near<0><<<tb, 128, 0, st>>>(d_txyz, d_tself, ntarg, d_bounds, d_node_off, npatch, eta, g, cell_cnt,
                                       cell_items, cnt, nullptr, nullptr);
+        RRQ_COUNT_LAUNCH();
+    }
     e = rrq_scan_exclusive(cnt, out->poff, ntarg, scan_tmp, st);
     if (e != cudaSuccess) return e;
     int64_t np_h = 0;
@@ -329,9 +346,11 @@ cudaError_t rrq_near_build(const double *d_bounds, int npatch, const int64_t *d_
     out->npairs = np_h;
     out->pairs = (int32_t *)alloc(actx, sizeof(int32_t) * (np_h > 0 ? np_h : 1));
     if (!out->pairs) return cudaErrorMemoryAllocation;
-    if (ntarg > 0)
+    if (ntarg > 0) {
         k_near<1><<<tb, 128, 0, st>>>(d_txyz, d_tself, ntarg, d_bounds, d_node_off, npatch, eta, g, cell_cnt,
                                       cell_items, nullptr, out->poff, out->pairs);
+        RRQ_COUNT_LAUNCH();
+    }
     return cudaGetLastError();
 }
 
@@ -356,16 +375,20 @@ cudaError_t rrq_items_build(const NearBuffers *nb, int64_t ntarg, const int32_t 
     if (!rowlen || !scan_tmp || !rcnt || !roff || !items) return cudaErrorMemoryAllocation;
     unsigned tb = (unsigned)((ntarg + 127) / 128);
     if (ntarg > 0) k_row_len<<<tb, 128, 0, st>>>(nb->poff, nb->pairs, ntarg, d_order, rowlen);
+    RRQ_COUNT_LAUNCH();
     cudaError_t e = rrq_scan_exclusive(rowlen, d_rowptr, ntarg, scan_tmp, st);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(rcnt, 0, sizeof(int64_t) * (npatch + 1), st);
-    if (nb->npairs > 0)
+    if (nb->npairs > 0) {
         k_rank_count<<<(unsigned)((nb->npairs + 255) / 256), 256, 0, st>>>(nb->pairs, nb->npairs, d_rank, rcnt);
+        RRQ_COUNT_LAUNCH();
+    }
     e = rrq_scan_exclusive(rcnt, roff, npatch, scan_tmp, st);
     if (e != cudaSuccess) return e;
     int64_t *cursor = rcnt;  // reuse
     cudaMemcpyAsync(cursor, roff, sizeof(int64_t) * (npatch + 1), cudaMemcpyDeviceToDevice, st);
     if (ntarg > 0) k_items<<<tb, 128, 0, st>>>(nb->poff, nb->pairs, ntarg, d_order, d_rowptr, d_rank, cursor, items);
+    RRQ_COUNT_LAUNCH();
     *items_out = items;
     *rank_off_out = roff;
     return cudaGetLastError();

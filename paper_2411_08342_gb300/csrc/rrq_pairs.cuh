@@ -659,6 +659,7 @@ cudaError_t launch_pairs_p(const OrderTables *d_tab, const PairItem *d_items, in
     k_pairs<P><<<(unsigned)grid, 32 * WARPS, bytes, st>>>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts,
                                                           d_txyz, d_tnrm, d_tself, mask, newton_max, vS, vD, vSp, vDp,
                                                           col, cnt);
+    RRQ_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 

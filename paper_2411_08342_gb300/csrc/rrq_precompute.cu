@@ -429,6 +429,7 @@ cudaError_t launch_pre(const OrderTables *d_tab, const int32_t *d_plist, int n, 
     if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
     k_precompute<P><<<n, 256, bytes, st>>>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd);
+    RRQ_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ class CSR(C.Structure):
 class Diag(C.Structure):
     _fields_ = [("npairs", C.c_int64), ("newton_fail", C.c_int64), ("on_edge", C.c_int64), ("u_poor", C.c_int64),
                 ("ssq_edges", C.c_int64), ("far_edges", C.c_int64), ("ms_near", C.c_double),
-                ("ms_precompute", C.c_double), ("ms_pairs", C.c_double)]
+                ("ms_precompute", C.c_double), ("ms_pairs", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 class RRQError(RuntimeError):
