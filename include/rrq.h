@@ -154,6 +154,36 @@ rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *t
 /* Counters and stage timings of the last rrq_build_corrections on this context. */
 rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag);
 
+/* Allocation-free build.  The paper has no counterpart to this entry point; it exists
+ * for callers that must not allocate device memory during a call: applications that
+ * reserve all device memory up front in their own allocator (a cudaMalloc would fail
+ * or fragment their pool), loops that forbid allocation after start-up, and plug-in
+ * hosts whose device footprint must not change once running.
+ *
+ * It computes exactly what rrq_build_corrections computes, with the same kernels, but
+ * takes every scratch buffer from one static device array of RRQ_STATIC_SCRATCH_BYTES
+ * (64 MiB) that each GPU loading this library holds until the process exits; about
+ * 0.35 MB per patch plus the near list fit in it (e.g. a few hundred patches), larger
+ * problems are rejected with RRQ_ERR_ARG and a message in rrq_last_error().  It calls
+ * no cudaMalloc, cudaFree or allocating library routine.
+ *   - inputs: device pointers only (inputs_on_host = 1 is rejected);
+ *   - outputs (device, caller-owned): rowptr [ntarg+1], col [capacity], val[k]
+ *     [capacity] for every kernel k in kernel_mask (S, D, S', D' order);
+ *   - *nnz_out and *npairs_out (host, may be NULL) receive the entry and pair counts;
+ *     when nnz exceeds capacity nothing is written to col/val and RRQ_ERR_ARG is
+ *     returned with *nnz_out set, so the caller can retry with larger buffers;
+ *   - the first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture;
+ *   - every call reuses the same array and leaves the last call's contents in it; what
+ *     must start at zero is cleared by each call.  Calls whose GPU work overlaps (two
+ *     streams, two threads, two contexts on one device) race on the array: serialise
+ *     them. */
+#define RRQ_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
+                                        uint32_t kernel_mask, const rrq_options *opt, int64_t *rowptr,
+                                        int32_t *col, double *val[4], int64_t capacity, int64_t *nnz_out,
+                                        int64_t *npairs_out);
+
 /* Measured fused-multiply-add throughput of this device in TFLOP/s (2 flops per FMA),
  * FP64 (fp32 = 0) or FP32 (fp32 = 1): 8 independent dependency chains per thread,
  * 8 blocks of 256 threads per SM, timed with CUDA events.  Used as the roofline

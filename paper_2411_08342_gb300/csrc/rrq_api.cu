@@ -597,3 +597,203 @@ extern "C" rrq_status rrq_measure_fma_peak(rrq_ctx *ctx, int32_t fp32, double *t
     CK(cudaSetDevice(ctx->device));
     return fp32 ? fma_peak<float>(ctx, tflops) : fma_peak<double>(ctx, tflops);
 }
+
+// ------------------------------------------------------------------------------------
+// Allocation-free variant of rrq_build_corrections.  All scratch (order tables, patch
+// data, near list, pair items, counters) lives in one file-scope device array that every
+// GPU loading this library keeps until the process exits; the caller provides the CSR
+// output buffers.  No cudaMalloc / cudaMallocAsync / cudaFree is called.
+// ------------------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_rrq_static_scratch[RRQ_STATIC_SCRATCH_BYTES];
+
+constexpr int RRQ_MAX_DEVICES = 64;
+static void *g_static_ptr[RRQ_MAX_DEVICES] = {nullptr};
+
+struct StaticArena {
+    unsigned char *base;
+    size_t used, cap;
+    bool failed;
+    size_t wanted;
+    static void *alloc(void *self, size_t bytes) {
+        StaticArena *a = static_cast<StaticArena *>(self);
+        size_t off = (a->used + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 16;
+        if (off + bytes > a->cap) {
+            a->failed = true;
+            a->wanted = off + bytes;
+            return nullptr;
+        }
+        a->used = off + bytes;
+        return a->base + off;
+    }
+};
+
+}  // namespace
+
+extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
+                                                   uint32_t kernel_mask, const rrq_options *opt, int64_t *rowptr,
+                                                   int32_t *col, double *val[4], int64_t capacity, int64_t *nnz_out,
+                                                   int64_t *npairs_out) {
+    if (!ctx || !rowptr || !col || !val || capacity < 0) return RRQ_ERR_ARG;
+    if (kernel_mask == 0 || (kernel_mask & ~15u)) return RRQ_ERR_ARG;
+    for (int k = 0; k < 4; k++)
+        if ((kernel_mask & (1u << k)) && !val[k]) return RRQ_ERR_ARG;
+    rrq_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.inputs_on_host) {
+        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: inputs must be device pointers");
+        return RRQ_ERR_ARG;
+    }
+    if (ctx->device < 0 || ctx->device >= RRQ_MAX_DEVICES) return RRQ_ERR_ARG;
+    const double eta = o.eta > 0 ? o.eta : 1.0;
+    const int newton_max = o.newton_max > 0 ? o.newton_max : 30;
+    CK(cudaSetDevice(ctx->device));
+    // set-up, once per device with that device current: device address of the array
+    if (!g_static_ptr[ctx->device]) {
+        void *p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_rrq_static_scratch));
+        g_static_ptr[ctx->device] = p;
+    }
+    memset(&ctx->diag, 0, sizeof(ctx->diag));
+    rrq_launch_counter() = 0;
+    StaticArena ar;
+    ar.base = static_cast<unsigned char *>(g_static_ptr[ctx->device]);
+    ar.used = 0;
+    ar.cap = RRQ_STATIC_SCRATCH_BYTES;
+    ar.failed = false;
+    ar.wanted = 0;
+    cudaStream_t st = ctx->stream;
+    // inputs (device pointers): sizes and orders read back to the host
+    if (!surf || surf->npatch < 1 || !surf->order || !surf->node_off || !surf->xyz || !surf->nrm || !surf->wts)
+        return RRQ_ERR_ARG;
+    if (!targ || targ->ntarg < 0 || (targ->ntarg > 0 && (!targ->xyz || !targ->nrm))) return RRQ_ERR_ARG;
+    const int npatch = surf->npatch;
+    const int64_t ntarg = targ->ntarg;
+    std::vector<int32_t> h_order(npatch);
+    std::vector<int64_t> h_node_off(npatch + 1);
+    CK(cudaMemcpyAsync(h_order.data(), surf->order, sizeof(int32_t) * npatch, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_node_off.data(), surf->node_off, sizeof(int64_t) * (npatch + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_node_off[0] != 0) return RRQ_ERR_ARG;
+    std::vector<std::vector<int32_t>> plist(RRQ_PMAX + 1);
+    int pmax = 0;
+    for (int P = 0; P < npatch; P++) {
+        int p = h_order[P];
+        if (p < 2 || p > RRQ_PMAX || !surf->ref_uv[p]) return RRQ_ERR_ARG;
+        if (h_node_off[P + 1] - h_node_off[P] != np_of(p)) return RRQ_ERR_ARG;
+        if (o.ptilde != 0 && o.ptilde != 2 * p) return RRQ_ERR_UNSUPPORTED;
+        plist[p].push_back(P);
+        pmax = std::max(pmax, p);
+    }
+    // order tables, built on the host and copied into the arena
+    OrderTables *tabs[RRQ_PMAX + 1] = {nullptr};
+    std::vector<OrderTables> htab(RRQ_PMAX + 1);
+    for (int p = 2; p <= RRQ_PMAX; p++)
+        if (!plist[p].empty()) {
+            if (rrq_host_order_tables(p, 2 * p, o.rho0, surf->ref_uv[p], &htab[p])) return RRQ_ERR_ARG;
+            tabs[p] = (OrderTables *)StaticArena::alloc(&ar, sizeof(OrderTables));
+            if (!tabs[p]) break;
+            CK(cudaMemcpyAsync(tabs[p], &htab[p], sizeof(OrderTables), cudaMemcpyHostToDevice, st));
+        }
+    const size_t NPc = npatch;
+    PatchData pd;
+    pd.npatch = npatch;
+    pd.pmax = pmax;
+    pd.frame = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * PD_FRAME);
+    pd.bounds = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * PD_BOUNDS);
+    pd.ynode = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ynode());
+    pd.ea = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ea());
+    pd.ey = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey());
+    pd.et = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey());
+    pd.eyu = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_eyu());
+    pd.eg = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg());
+    pd.eh = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg());
+    pd.XD = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
+    pd.XSp = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
+    pd.XS2 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
+    pd.XS1 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_XS1());
+    pd.status = (int *)StaticArena::alloc(&ar, sizeof(int) * NPc);
+    int32_t *d_plists = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);
+    int32_t *d_rank = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);
+    BuildCounters *d_cnt = (BuildCounters *)StaticArena::alloc(&ar, sizeof(BuildCounters));
+    if (ar.failed) {
+        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
+                 ar.wanted, (size_t)RRQ_STATIC_SCRATCH_BYTES);
+        return RRQ_ERR_ARG;
+    }
+    std::vector<int32_t> rank(npatch), order_major;
+    order_major.reserve(npatch);
+    for (int p = 2; p <= RRQ_PMAX; p++)
+        for (int32_t P : plist[p]) order_major.push_back(P);
+    for (int r = 0; r < npatch; r++) rank[order_major[r]] = r;
+    CK(cudaMemcpyAsync(d_plists, order_major.data(), sizeof(int32_t) * npatch, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_rank, rank.data(), sizeof(int32_t) * npatch, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(BuildCounters), st));
+    {
+        int start = 0;
+        for (int p = 2; p <= RRQ_PMAX; p++) {
+            int n = (int)plist[p].size();
+            if (n) CK(rrq_launch_precompute(p, tabs[p], d_plists + start, n, surf->node_off, surf->xyz, surf->nrm, pd, st));
+            start += n;
+        }
+    }
+    NearBuffers nb;
+    cudaError_t e = rrq_near_build(pd.bounds, npatch, surf->node_off, targ->xyz, targ->self_node, ntarg, eta,
+                                   &StaticArena::alloc, &ar, &nb, st);
+    PairItem *items = nullptr;
+    int64_t *roff = nullptr;
+    if (e == cudaSuccess && !ar.failed)
+        e = rrq_items_build(&nb, ntarg, surf->order, d_rank, npatch, &StaticArena::alloc, &ar, rowptr, &items, &roff, st);
+    if (ar.failed) {
+        cudaStreamSynchronize(st);
+        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
+                 ar.wanted, (size_t)RRQ_STATIC_SCRATCH_BYTES);
+        return RRQ_ERR_ARG;
+    }
+    CK(e);
+    int64_t nnz = 0;
+    std::vector<int64_t> h_roff(npatch + 1);
+    std::vector<int> h_status(npatch);
+    CK(cudaMemcpyAsync(&nnz, rowptr + ntarg, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_roff.data(), roff, sizeof(int64_t) * (npatch + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_status.data(), pd.status, sizeof(int) * npatch, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (nnz_out) *nnz_out = nnz;
+    if (npairs_out) *npairs_out = nb.npairs;
+    for (int P = 0; P < npatch; P++)
+        if (h_status[P]) return RRQ_ERR_DEGENERATE;
+    if (nnz > capacity) {
+        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: %lld entries exceed the output capacity %lld",
+                 (long long)nnz, (long long)capacity);
+        return RRQ_ERR_ARG;
+    }
+    {
+        int start = 0;
+        for (int p = 2; p <= RRQ_PMAX; p++) {
+            int n = (int)plist[p].size();
+            if (n) {
+                int64_t i0 = h_roff[start], i1 = h_roff[start + n];
+                CK(rrq_launch_pairs(p, tabs[p], items + i0, i1 - i0, pd, surf->node_off, surf->xyz, surf->nrm,
+                                    surf->wts, targ->xyz, targ->nrm, targ->self_node, kernel_mask, newton_max,
+                                    (kernel_mask & RRQ_S) ? val[0] : nullptr, (kernel_mask & RRQ_D) ? val[1] : nullptr,
+                                    (kernel_mask & RRQ_SP) ? val[2] : nullptr,
+                                    (kernel_mask & RRQ_DP) ? val[3] : nullptr, col, d_cnt, st));
+            }
+            start += n;
+        }
+    }
+    BuildCounters hc;
+    CK(cudaMemcpyAsync(&hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->diag.npairs = nb.npairs;
+    ctx->diag.newton_fail = (int64_t)hc.newton_fail;
+    ctx->diag.on_edge = (int64_t)hc.on_edge;
+    ctx->diag.u_poor = (int64_t)hc.u_poor;
+    ctx->diag.ssq_edges = (int64_t)hc.ssq_edges;
+    ctx->diag.far_edges = (int64_t)hc.far_edges;
+    ctx->diag.kernel_launches = rrq_launch_counter();
+    return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
+}

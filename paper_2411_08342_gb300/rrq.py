@@ -77,6 +77,10 @@ def load(build_if_needed: bool = True):
                                     C.c_void_p, C.c_void_p, C.POINTER(Options)]
             L.rrq_last_diagnostics.argtypes = [C.c_void_p, C.POINTER(Diag)]
             L.rrq_measure_fma_peak.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]
+            L.rrq_build_corrections_static.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS),
+                                                       C.c_uint32, C.POINTER(Options), C.c_void_p, C.c_void_p,
+                                                       C.c_void_p * 4, C.c_int64, C.POINTER(C.c_int64),
+                                                       C.POINTER(C.c_int64)]
             _lib = L
     return _lib
 
@@ -158,6 +162,24 @@ class Context:
         _check(st, "rrq_build_corrections")
         self.last_status = st
         return out
+
+    def build_corrections_static(self, surf: Surface, targ: TargetsS, rowptr, col, vals: dict,
+                                 kernels=("S", "D", "SP", "DP")):
+        """Allocation-free build into caller-owned device buffers (torch CUDA tensors):
+        rowptr [ntarg+1] int64, col [capacity] int32, vals {kernel: [capacity] float64}.
+        Returns (nnz, npairs)."""
+        mask = 0
+        arr = (C.c_void_p * 4)()
+        for k in kernels:
+            mask |= KERNEL_BITS[k]
+            arr[KERNEL_SLOT[k]] = vals[k].data_ptr()
+        cap = int(col.shape[0])
+        nnz, npairs = C.c_int64(), C.c_int64()
+        opt = Options(0, 0, 0.0, 0, 0.0)
+        st = self.L.rrq_build_corrections_static(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt),
+                                                 _ptr(rowptr), _ptr(col), arr, cap, C.byref(nnz), C.byref(npairs))
+        _check(st, "rrq_build_corrections_static")
+        return nnz.value, npairs.value
 
     def csr_free(self, csr: CSR):
         _check(self.L.rrq_csr_free(self.h, C.byref(csr)), "rrq_csr_free")
