@@ -55,6 +55,7 @@ struct OrderTables {
     double LegW[RRQ_PMAX * RRQ_PTMAX];              // [n][q] (2n+1)/2 w_q P_n(t_q)
     double dLeg[RRQ_PTMAX * RRQ_PMAX];              // [q][n] P_n'(t_q)
     double LegU[2 * RRQ_PTMAX * RRQ_PMAX];          // [s][n] P_n(tu_s)
+    double L2M[RRQ_PMAX * RRQ_PMAX];                // [n][k] coefficient of t^k in P_n(t)
 };
 
 // Device-side per-patch data (strides sized for the largest order of the surface).

@@ -49,7 +49,9 @@ struct PairSm {
     static constexpr int B = OM + 8;                                  // NP*4
     static constexpr int BD = B + 4 * NP;                             // NP*4
     static constexpr int PSI = BD + 4 * NP;                           // NP
-    static constexpr int TOTAL = PSI + NP + 2;
+    static constexpr int WV = PSI + NP;                               // NS*12 premultiplied sample vectors
+    static constexpr int EM = WV + 12 * NS;                           // 3*P*3 monomial edge coefficients
+    static constexpr int TOTAL = EM + 9 * P + 2;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -105,6 +107,12 @@ __device__ __forceinline__ cd kflip(cd v, int k) {
     v.y = -v.y;
     if ((-k) & 1) { v.x = -v.x; v.y = -v.y; }
     return v;
+}
+
+// acc += a * b (complex), as four fused multiply-adds
+__device__ __forceinline__ void cfma(cd &acc, const cd a, const cd b) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
 }
 
 __device__ __forceinline__ void edge_eval_real(const double *ea, int p, double t, double y[3], double dy[3]) {
@@ -254,7 +262,17 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
         double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
         cd tt = mkc((b[0] * w[0] + b[1] * w[1] + b[2] * w[2]) / bb, sqrt(bw0 * bw0 + bw1 * bw1 + bw2 * bw2) / bb);
         int conv = 0;
-        for (int it = 0; it < newton_max; it++) {
+        // an edge whose chord root lies well outside the Bernstein ellipse rho0 takes the
+        // upsampled rule whatever the exact root is: the root is not refined
+        bool skip = false;
+        {
+            cd zm1 = mkc(tt.x - 1.0, tt.y), zp1 = mkc(tt.x + 1.0, tt.y);
+            cd wv = cadd(tt, cmul(sqrt_c(zm1), sqrt_c(zp1)));
+            double rc = sqrt(cabs2(wv));
+            if (rc < 1.0) rc = 1.0 / rc;
+            if (rc > 1.5 * tab->rho0 && tt.y > 0.0) { skip = true; conv = 1; }
+        }
+        for (int it = 0; it < (skip ? 0 : newton_max); it++) {
             cd y[3], dy[3];
             edge_eval_cplx(ce, P, tt, y, dy);
             cd g = mkc(0, 0), gp = mkc(0, 0);
@@ -343,11 +361,20 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
             __syncwarp();
         }
     }
+    // monomial coefficients of the three edges (for Horner evaluation on the panels)
+    double *em = sw + Z::EM;
+    for (int w = lane; w < 9 * P; w += 32) {
+        const int e = w / (3 * P), rem = w % (3 * P), k = rem / 3, a = rem % 3;
+        double v = 0.0;
+        for (int n = k; n < P; n++) v = fma(ea[(e * P + n) * 3 + a], tab->L2M[n * P + k], v);
+        em[w] = v;
+    }
+    __syncwarp();
     // Omega_0 and d Omega_0 / d nu' on graded panels
     double o0 = 0.0, do0 = 0.0;
     const double nxu0 = uz * nut[1], nxu1 = -uz * nut[0], nuu = nut[2] * uz;
     for (int e = 0; e < 3; e++) {
-        const double *ce = ea + 3 * P * e;
+        const double *cm = em + 3 * P * e;
         const double tr = t0s[4 * e], ti = t0s[4 * e + 1];
         double c, sig;
         if (t0s[4 * e + 2] != 0.0) {
@@ -370,7 +397,7 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
             if (pan < nl) {
                 int k = nl - pan;  // left panel k: [y_k, y_{k-1}]
                 double yk = lo, len = sig, ykm1 = lo;
-                for (int s = 1; s <= k; s++) { ykm1 = yk; yk -= len; len *= 2; }
+                for (int s2 = 1; s2 <= k; s2++) { ykm1 = yk; yk -= len; len *= 2; }
                 a0 = fmax(yk, -1.0);
                 a1 = ykm1;
             } else if (pan == nl) {
@@ -379,24 +406,29 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
             } else {
                 int k = pan - nl;
                 double xk = hi, len = sig, xkm1 = hi;
-                for (int s = 1; s <= k; s++) { xkm1 = xk; xk += len; len *= 2; }
+                for (int s2 = 1; s2 <= k; s2++) { xkm1 = xk; xk += len; len *= 2; }
                 a0 = xkm1;
                 a1 = fmin(xk, 1.0);
             }
             const double mid = 0.5 * (a0 + a1), half = 0.5 * (a1 - a0);
-            const double tt = mid + half * tab->tom[g], wg = half * tab->wom[g];
-            double y[3], dy[3];
-            edge_eval_real(ce, P, tt, y, dy);
-            const double d0 = yt[0] - y[0], d1 = yt[1] - y[1], d2 = yt[2] - y[2];
-            const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-            const double E = r + uz * d2;
-            const double N = uz * (d1 * dy[0] - d0 * dy[1]);
-            o0 -= wg * N / (r * E);
+            const double tt = fma(half, tab->tom[g], mid), wg = half * tab->wom[g];
+            double y0 = cm[3 * (P - 1)], y1 = cm[3 * (P - 1) + 1], y2 = cm[3 * (P - 1) + 2];
+            double dy0 = 0.0, dy1 = 0.0, dy2 = 0.0;
+            for (int k = P - 2; k >= 0; k--) {
+                dy0 = fma(dy0, tt, y0); dy1 = fma(dy1, tt, y1); dy2 = fma(dy2, tt, y2);
+                y0 = fma(y0, tt, cm[3 * k]); y1 = fma(y1, tt, cm[3 * k + 1]); y2 = fma(y2, tt, cm[3 * k + 2]);
+            }
+            const double d0 = yt[0] - y0, d1 = yt[1] - y1, d2 = yt[2] - y2;
+            const double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+            const double ir = rsqrt(r2), r = r2 * ir;
+            const double E = fma(uz, d2, r);
+            const double iE = 1.0 / E, inv = ir * iE;
+            const double N = uz * (d1 * dy0 - d0 * dy1);
+            o0 = fma(-wg * N, inv, o0);
             if (wantDP) {
-                const double nd = nut[0] * d0 + nut[1] * d1 + nut[2] * d2;
-                const double v = (nxu0 * dy[0] + nxu1 * dy[1]) / (r * E) - nuu * N / (r * E * E) -
-                                 nd * N / (r * r * E * E) - nd * N / (r * r * r * E);
-                do0 -= wg * v;
+                const double nd = fma(nut[0], d0, fma(nut[1], d1, nut[2] * d2));
+                const double v = inv * ((nxu0 * dy0 + nxu1 * dy1) - N * iE * (nuu + nd * ir) - nd * N * ir * ir);
+                do0 = fma(-wg, v, do0);
             }
         }
     }
@@ -419,50 +451,64 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
         Om[0] = o0; Om[1] = ov[0]; Om[2] = ov[1]; Om[3] = ov[2];
         Om[4] = do0; Om[5] = dov[0]; Om[6] = dov[1]; Om[7] = dov[2];
     }
+    // per-sample premultiplied vectors: w1 d, w1 (tau x d), w1 nu', w3 (nu'.d) d
+    double *wv = sw + Z::WV;
+    for (int q = lane; q < NS; q += 32) {
+        const double w1 = om1[q], w3 = om3[q];
+        const double d0 = dq[3 * q], d1 = dq[3 * q + 1], d2 = dq[3 * q + 2];
+        const double t0 = tau[3 * q], t1 = tau[3 * q + 1], t2 = tau[3 * q + 2];
+        const double w3n = w3 * (nut[0] * d0 + nut[1] * d1 + nut[2] * d2);
+        double *o = wv + 12 * q;
+        o[0] = w1 * d0; o[1] = w1 * d1; o[2] = w1 * d2;
+        o[3] = w1 * (t1 * d2 - t2 * d1); o[4] = w1 * (t2 * d0 - t0 * d2); o[5] = w1 * (t0 * d1 - t1 * d0);
+        o[6] = w1 * nut[0]; o[7] = w1 * nut[1]; o[8] = w1 * nut[2];
+        o[9] = w3n * d0; o[10] = w3n * d1; o[11] = w3n * d2;
+    }
+    __syncwarp();
     // Step 6: line integrals, one lane per (j, k >= 0), j >= 1
     const cd *eg = pd.eg + ps * pd_eg();
     const cd *eh = pd.eh + ps * pd_eg();
     for (int jk = 1 + lane; jk < NJK; jk += 32) {
-        int j = 0;
-        while (jk_index(j + 1, 0) <= jk) j++;
-        cd V = mkc(0, 0), Q0 = mkc(0, 0), Q1 = mkc(0, 0), Q2 = mkc(0, 0), Q3 = mkc(0, 0);
-        cd D0 = mkc(0, 0), D1 = mkc(0, 0), D2 = mkc(0, 0), D3 = mkc(0, 0);
+        const bool hj = jk >= 3;  // j >= 2
+        double Vr = 0, Vi = 0;
+        double Q0r = 0, Q0i = 0, Q1r = 0, Q1i = 0, Q2r = 0, Q2i = 0, Q3r = 0, Q3i = 0;
+        double D0r = 0, D0i = 0, D1r = 0, D1i = 0, D2r = 0, D2i = 0, D3r = 0, D3i = 0;
         for (int q = 0; q < NS; q++) {
-            const double w1 = om1[q];
-            const double d0 = dq[3 * q], d1 = dq[3 * q + 1], d2 = dq[3 * q + 2];
-            const double t0 = tau[3 * q], t1 = tau[3 * q + 1], t2 = tau[3 * q + 2];
+            const double *o = wv + 12 * q;
             const cd *g = eg + ((size_t)q * NJK + jk) * 3;
             const cd g0 = g[0], g1 = g[1], g2 = g[2];
-            // (d x g) . tau = g . (tau x d)
-            const double c0 = t1 * d2 - t2 * d1, c1 = t2 * d0 - t0 * d2, c2 = t0 * d1 - t1 * d0;
-            V = cadd(V, cscale(cadd(cadd(cscale(g0, c0), cscale(g1, c1)), cscale(g2, c2)), w1));
-            if (j >= 2) {
+            Vr = fma(g0.x, o[3], fma(g1.x, o[4], fma(g2.x, o[5], Vr)));
+            Vi = fma(g0.y, o[3], fma(g1.y, o[4], fma(g2.y, o[5], Vi)));
+            if (hj) {
                 const cd *h = eh + ((size_t)q * NJK + jk) * 3;
                 const cd h0 = h[0], h1 = h[1], h2 = h[2];
-                const cd dh = cadd(cadd(cscale(h0, d0), cscale(h1, d1)), cscale(h2, d2));
-                const cd x0 = csub(cscale(h2, d1), cscale(h1, d2));
-                const cd x1 = csub(cscale(h0, d2), cscale(h2, d0));
-                const cd x2 = csub(cscale(h1, d0), cscale(h0, d1));
-                Q0 = csub(Q0, cscale(dh, w1));
-                Q1 = cadd(Q1, cscale(x0, w1));
-                Q2 = cadd(Q2, cscale(x1, w1));
-                Q3 = cadd(Q3, cscale(x2, w1));
+                const double a0 = o[0], a1 = o[1], a2 = o[2];
+                // (0, w1 d)(0, h) = (-(w1 d).h, (w1 d) x h)
+                Q0r = fma(-a0, h0.x, fma(-a1, h1.x, fma(-a2, h2.x, Q0r)));
+                Q0i = fma(-a0, h0.y, fma(-a1, h1.y, fma(-a2, h2.y, Q0i)));
+                Q1r = fma(a1, h2.x, fma(-a2, h1.x, Q1r));
+                Q1i = fma(a1, h2.y, fma(-a2, h1.y, Q1i));
+                Q2r = fma(a2, h0.x, fma(-a0, h2.x, Q2r));
+                Q2i = fma(a2, h0.y, fma(-a0, h2.y, Q2i));
+                Q3r = fma(a0, h1.x, fma(-a1, h0.x, Q3r));
+                Q3i = fma(a0, h1.y, fma(-a1, h0.y, Q3i));
                 if (wantDP) {
-                    const double w3n = om3[q] * (nut[0] * d0 + nut[1] * d1 + nut[2] * d2);
-                    const cd nh = cadd(cadd(cscale(h0, nut[0]), cscale(h1, nut[1])), cscale(h2, nut[2]));
-                    const cd y0 = csub(cscale(h2, nut[1]), cscale(h1, nut[2]));
-                    const cd y1 = csub(cscale(h0, nut[2]), cscale(h2, nut[0]));
-                    const cd y2 = csub(cscale(h1, nut[0]), cscale(h0, nut[1]));
-                    D0 = cadd(D0, csub(cscale(dh, w3n), cscale(nh, w1)));
-                    D1 = cadd(D1, csub(cscale(y0, w1), cscale(x0, w3n)));
-                    D2 = cadd(D2, csub(cscale(y1, w1), cscale(x1, w3n)));
-                    D3 = cadd(D3, csub(cscale(y2, w1), cscale(x2, w3n)));
+                    // w1 (0,nu')(0,h) - w3 (nu'.d) (0,d)(0,h)
+                    const double n0 = o[6], n1 = o[7], n2 = o[8], m0 = o[9], m1 = o[10], m2 = o[11];
+                    D0r = fma(m0, h0.x, fma(m1, h1.x, fma(m2, h2.x, fma(-n0, h0.x, fma(-n1, h1.x, fma(-n2, h2.x, D0r))))));
+                    D0i = fma(m0, h0.y, fma(m1, h1.y, fma(m2, h2.y, fma(-n0, h0.y, fma(-n1, h1.y, fma(-n2, h2.y, D0i))))));
+                    D1r = fma(n1, h2.x, fma(-n2, h1.x, fma(-m1, h2.x, fma(m2, h1.x, D1r))));
+                    D1i = fma(n1, h2.y, fma(-n2, h1.y, fma(-m1, h2.y, fma(m2, h1.y, D1i))));
+                    D2r = fma(n2, h0.x, fma(-n0, h2.x, fma(-m2, h0.x, fma(m0, h2.x, D2r))));
+                    D2i = fma(n2, h0.y, fma(-n0, h2.y, fma(-m2, h0.y, fma(m0, h2.y, D2i))));
+                    D3r = fma(n0, h1.x, fma(-n1, h0.x, fma(-m0, h1.x, fma(m1, h0.x, D3r))));
+                    D3i = fma(n0, h1.y, fma(-n1, h0.y, fma(-m0, h1.y, fma(m1, h0.y, D3i))));
                 }
             }
         }
-        Vs[jk] = V;
-        Qs[4 * jk] = Q0; Qs[4 * jk + 1] = Q1; Qs[4 * jk + 2] = Q2; Qs[4 * jk + 3] = Q3;
-        dQs[4 * jk] = D0; dQs[4 * jk + 1] = D1; dQs[4 * jk + 2] = D2; dQs[4 * jk + 3] = D3;
+        Vs[jk] = mkc(Vr, Vi);
+        Qs[4 * jk] = mkc(Q0r, Q0i); Qs[4 * jk + 1] = mkc(Q1r, Q1i); Qs[4 * jk + 2] = mkc(Q2r, Q2i); Qs[4 * jk + 3] = mkc(Q3r, Q3i);
+        dQs[4 * jk] = mkc(D0r, D0i); dQs[4 * jk + 1] = mkc(D1r, D1i); dQs[4 * jk + 2] = mkc(D2r, D2i); dQs[4 * jk + 3] = mkc(D3r, D3i);
     }
     __syncwarp();
     // Step 7: translations, one lane per (l, m), 1 <= m <= l <= P
@@ -484,15 +530,15 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
                 const int ak = k < 0 ? -k : k;
                 const int jkx = jk_index(j, ak);
                 const cd Sv = tget(St, l - j, m - k);
-                Ip = cadd(Ip, cscale(cmul(kflip(Vs[jkx], k), Sv), Dj));
+                cfma(Ip, kflip(Vs[jkx], k), cscale(Sv, Dj));
                 if (j >= 2) {
                     const cd q0 = kflip(Qs[4 * jkx], k), q1 = kflip(Qs[4 * jkx + 1], k);
                     const cd q2 = kflip(Qs[4 * jkx + 2], k), q3 = kflip(Qs[4 * jkx + 3], k);
                     const cd cs = cscale(Sv, Cj);
-                    Ib0 = cadd(Ib0, cmul(q0, cs));
-                    Ib1 = cadd(Ib1, cmul(q1, cs));
-                    Ib2 = cadd(Ib2, cmul(q2, cs));
-                    Ib3 = cadd(Ib3, cmul(q3, cs));
+                    cfma(Ib0, q0, cs);
+                    cfma(Ib1, q1, cs);
+                    cfma(Ib2, q2, cs);
+                    cfma(Ib3, q3, cs);
                     if (wantDP) {
                         // d/dnu' of S^{(l-j, m-k)}(y') = grad . nu'
                         const int n = l - j, qq = m - k, aq = qq < 0 ? -qq : qq;
@@ -503,10 +549,14 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
                             dS = kflip(dS, qq);
                         }
                         const cd cd2 = cscale(dS, Cj);
-                        dI0 = cadd(dI0, cadd(cmul(kflip(dQs[4 * jkx], k), cs), cmul(q0, cd2)));
-                        dI1 = cadd(dI1, cadd(cmul(kflip(dQs[4 * jkx + 1], k), cs), cmul(q1, cd2)));
-                        dI2 = cadd(dI2, cadd(cmul(kflip(dQs[4 * jkx + 2], k), cs), cmul(q2, cd2)));
-                        dI3 = cadd(dI3, cadd(cmul(kflip(dQs[4 * jkx + 3], k), cs), cmul(q3, cd2)));
+                        cfma(dI0, kflip(dQs[4 * jkx], k), cs);
+                        cfma(dI0, q0, cd2);
+                        cfma(dI1, kflip(dQs[4 * jkx + 1], k), cs);
+                        cfma(dI1, q1, cd2);
+                        cfma(dI2, kflip(dQs[4 * jkx + 2], k), cs);
+                        cfma(dI2, q2, cd2);
+                        cfma(dI3, kflip(dQs[4 * jkx + 3], k), cs);
+                        cfma(dI3, q3, cd2);
                     }
                 }
             }

@@ -208,5 +208,15 @@ int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, Orde
         legendre_vals(p, T->tu[s], P, dP);
         for (int n = 0; n < p; n++) T->LegU[s * p + n] = P[n];
     }
+    // monomial coefficients of P_n by (n+1) P_{n+1} = (2n+1) t P_n - n P_{n-1}
+    for (int i = 0; i < p * p; i++) T->L2M[i] = 0.0;
+    T->L2M[0] = 1.0;
+    if (p > 1) T->L2M[1 * p + 1] = 1.0;
+    for (int n = 1; n + 1 < p; n++)
+        for (int k = 0; k < p; k++) {
+            double v = -(double)n * T->L2M[(n - 1) * p + k];
+            if (k > 0) v += (2.0 * n + 1.0) * T->L2M[n * p + k - 1];
+            T->L2M[(n + 1) * p + k] = v / (n + 1.0);
+        }
     return 0;
 }
