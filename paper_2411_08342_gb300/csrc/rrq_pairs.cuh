@@ -473,6 +473,7 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
         double Vr = 0, Vi = 0;
         double Q0r = 0, Q0i = 0, Q1r = 0, Q1i = 0, Q2r = 0, Q2i = 0, Q3r = 0, Q3i = 0;
         double D0r = 0, D0i = 0, D1r = 0, D1i = 0, D2r = 0, D2i = 0, D3r = 0, D3i = 0;
+        double E0r = 0, E0i = 0, E1r = 0, E1i = 0, E2r = 0, E2i = 0, E3r = 0, E3i = 0;
         for (int q = 0; q < NS; q++) {
             const double *o = wv + 12 * q;
             const cd *g = eg + ((size_t)q * NJK + jk) * 3;
@@ -493,18 +494,31 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
                 Q3r = fma(a0, h1.x, fma(-a1, h0.x, Q3r));
                 Q3i = fma(a0, h1.y, fma(-a1, h0.y, Q3i));
                 if (wantDP) {
-                    // w1 (0,nu')(0,h) - w3 (nu'.d) (0,d)(0,h)
-                    const double n0 = o[6], n1 = o[7], n2 = o[8], m0 = o[9], m1 = o[10], m2 = o[11];
-                    D0r = fma(m0, h0.x, fma(m1, h1.x, fma(m2, h2.x, fma(-n0, h0.x, fma(-n1, h1.x, fma(-n2, h2.x, D0r))))));
-                    D0i = fma(m0, h0.y, fma(m1, h1.y, fma(m2, h2.y, fma(-n0, h0.y, fma(-n1, h1.y, fma(-n2, h2.y, D0i))))));
-                    D1r = fma(n1, h2.x, fma(-n2, h1.x, fma(-m1, h2.x, fma(m2, h1.x, D1r))));
-                    D1i = fma(n1, h2.y, fma(-n2, h1.y, fma(-m1, h2.y, fma(m2, h1.y, D1i))));
-                    D2r = fma(n2, h0.x, fma(-n0, h2.x, fma(-m2, h0.x, fma(m0, h2.x, D2r))));
-                    D2i = fma(n2, h0.y, fma(-n0, h2.y, fma(-m2, h0.y, fma(m0, h2.y, D2i))));
-                    D3r = fma(n0, h1.x, fma(-n1, h0.x, fma(-m0, h1.x, fma(m1, h0.x, D3r))));
-                    D3i = fma(n0, h1.y, fma(-n1, h0.y, fma(-m0, h1.y, fma(m1, h0.y, D3i))));
+                    // sum_q w1 h (the nu' factor is applied after the sum) and
+                    // sum_q w3 (nu'.d) (0,d)(0,h)
+                    const double w1 = om1[q], m0 = o[9], m1 = o[10], m2 = o[11];
+                    D0r = fma(w1, h0.x, D0r); D0i = fma(w1, h0.y, D0i);     // H1 (3 complex, in D0..D2)
+                    D1r = fma(w1, h1.x, D1r); D1i = fma(w1, h1.y, D1i);
+                    D2r = fma(w1, h2.x, D2r); D2i = fma(w1, h2.y, D2i);
+                    E0r = fma(-m0, h0.x, fma(-m1, h1.x, fma(-m2, h2.x, E0r)));
+                    E0i = fma(-m0, h0.y, fma(-m1, h1.y, fma(-m2, h2.y, E0i)));
+                    E1r = fma(m1, h2.x, fma(-m2, h1.x, E1r));
+                    E1i = fma(m1, h2.y, fma(-m2, h1.y, E1i));
+                    E2r = fma(m2, h0.x, fma(-m0, h2.x, E2r));
+                    E2i = fma(m2, h0.y, fma(-m0, h2.y, E2i));
+                    E3r = fma(m0, h1.x, fma(-m1, h0.x, E3r));
+                    E3i = fma(m0, h1.y, fma(-m1, h0.y, E3i));
                 }
             }
+        }
+        if (wantDP) {
+            // dQ = (0,nu')(0,H1) - (0, w3 (nu'.d) d)(0,h) summed
+            const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
+            const double a0 = -(n0 * D0r + n1 * D1r + n2 * D2r) - E0r, b0 = -(n0 * D0i + n1 * D1i + n2 * D2i) - E0i;
+            const double a1 = (n1 * D2r - n2 * D1r) - E1r, b1 = (n1 * D2i - n2 * D1i) - E1i;
+            const double a2 = (n2 * D0r - n0 * D2r) - E2r, b2 = (n2 * D0i - n0 * D2i) - E2i;
+            const double a3 = (n0 * D1r - n1 * D0r) - E3r, b3 = (n0 * D1i - n1 * D0i) - E3i;
+            D0r = a0; D0i = b0; D1r = a1; D1i = b1; D2r = a2; D2i = b2; D3r = a3; D3i = b3;
         }
         Vs[jk] = mkc(Vr, Vi);
         Qs[4 * jk] = mkc(Q0r, Q0i); Qs[4 * jk + 1] = mkc(Q1r, Q1i); Qs[4 * jk + 2] = mkc(Q2r, Q2i); Qs[4 * jk + 3] = mkc(Q3r, Q3i);
@@ -520,8 +534,8 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
         int l = 1;
         while ((l + 1) * l / 2 <= lm) l++;
         const int m = lm - l * (l - 1) / 2 + 1;
-        cd Ib0 = mkc(0, 0), Ib1 = mkc(0, 0), Ib2 = mkc(0, 0), Ib3 = mkc(0, 0), Ip = mkc(0, 0);
-        cd dI0 = mkc(0, 0), dI1 = mkc(0, 0), dI2 = mkc(0, 0), dI3 = mkc(0, 0);
+        // only imaginary parts are needed (B = sqrt2 Im(...)): Im(a b) = a.x b.y + a.y b.x
+        double Ib0 = 0, Ib1 = 0, Ib2 = 0, Ib3 = 0, Ip = 0, dI0 = 0, dI1 = 0, dI2 = 0, dI3 = 0;
         for (int j = 1; j <= l; j++) {
             const double Dj = FACT[j - 1] * FACT[l - j] / FACT[l];
             const double Cj = j >= 2 ? FACT[j - 2] * FACT[l - j] / FACT[l - 1] : 0.0;
@@ -530,15 +544,16 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
                 const int ak = k < 0 ? -k : k;
                 const int jkx = jk_index(j, ak);
                 const cd Sv = tget(St, l - j, m - k);
-                cfma(Ip, kflip(Vs[jkx], k), cscale(Sv, Dj));
+                const cd v = kflip(Vs[jkx], k);
+                Ip = fma(Dj, fma(v.x, Sv.y, v.y * Sv.x), Ip);
                 if (j >= 2) {
                     const cd q0 = kflip(Qs[4 * jkx], k), q1 = kflip(Qs[4 * jkx + 1], k);
                     const cd q2 = kflip(Qs[4 * jkx + 2], k), q3 = kflip(Qs[4 * jkx + 3], k);
                     const cd cs = cscale(Sv, Cj);
-                    cfma(Ib0, q0, cs);
-                    cfma(Ib1, q1, cs);
-                    cfma(Ib2, q2, cs);
-                    cfma(Ib3, q3, cs);
+                    Ib0 = fma(q0.x, cs.y, fma(q0.y, cs.x, Ib0));
+                    Ib1 = fma(q1.x, cs.y, fma(q1.y, cs.x, Ib1));
+                    Ib2 = fma(q2.x, cs.y, fma(q2.y, cs.x, Ib2));
+                    Ib3 = fma(q3.x, cs.y, fma(q3.y, cs.x, Ib3));
                     if (wantDP) {
                         // d/dnu' of S^{(l-j, m-k)}(y') = grad . nu'
                         const int n = l - j, qq = m - k, aq = qq < 0 ? -qq : qq;
@@ -548,15 +563,13 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
                             dS = cadd(cadd(cscale(gg[0], nut[0]), cscale(gg[1], nut[1])), cscale(gg[2], nut[2]));
                             dS = kflip(dS, qq);
                         }
-                        const cd cd2 = cscale(dS, Cj);
-                        cfma(dI0, kflip(dQs[4 * jkx], k), cs);
-                        cfma(dI0, q0, cd2);
-                        cfma(dI1, kflip(dQs[4 * jkx + 1], k), cs);
-                        cfma(dI1, q1, cd2);
-                        cfma(dI2, kflip(dQs[4 * jkx + 2], k), cs);
-                        cfma(dI2, q2, cd2);
-                        cfma(dI3, kflip(dQs[4 * jkx + 3], k), cs);
-                        cfma(dI3, q3, cd2);
+                        const cd c2 = cscale(dS, Cj);
+                        const cd e0 = kflip(dQs[4 * jkx], k), e1 = kflip(dQs[4 * jkx + 1], k);
+                        const cd e2 = kflip(dQs[4 * jkx + 2], k), e3 = kflip(dQs[4 * jkx + 3], k);
+                        dI0 = fma(e0.x, cs.y, fma(e0.y, cs.x, fma(q0.x, c2.y, fma(q0.y, c2.x, dI0))));
+                        dI1 = fma(e1.x, cs.y, fma(e1.y, cs.x, fma(q1.x, c2.y, fma(q1.y, c2.x, dI1))));
+                        dI2 = fma(e2.x, cs.y, fma(e2.y, cs.x, fma(q2.x, c2.y, fma(q2.y, c2.x, dI2))));
+                        dI3 = fma(e3.x, cs.y, fma(e3.y, cs.x, fma(q3.x, c2.y, fma(q3.y, c2.x, dI3))));
                     }
                 }
             }
@@ -569,12 +582,12 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
         const cd G2 = cadd(cscale(g[1], W0), csub(cscale(g[0], W3), cscale(g[2], W1)));
         const cd G3 = cadd(cscale(g[2], W0), csub(cscale(g[1], W1), cscale(g[0], W2)));
         const double f = sq2 * inv4pi;
-        Bs[4 * lm] = f * (Ib0.y + G0.y);
-        Bs[4 * lm + 1] = f * (Ib1.y + G1.y);
-        Bs[4 * lm + 2] = f * (Ib2.y + G2.y);
-        Bs[4 * lm + 3] = f * (Ib3.y + G3.y);
+        Bs[4 * lm] = f * (Ib0 + G0.y);
+        Bs[4 * lm + 1] = f * (Ib1 + G1.y);
+        Bs[4 * lm + 2] = f * (Ib2 + G2.y);
+        Bs[4 * lm + 3] = f * (Ib3 + G3.y);
         const cd Slm = St[jk_index(l, m)];
-        Psis[lm] = f * (Ip.y + Slm.y * Om[0]);
+        Psis[lm] = f * (Ip + Slm.y * Om[0]);
         if (wantDP) {
             const double X0 = Om[4], X1 = Om[5], X2 = Om[6], X3 = Om[7];
             const cd E0 = cscale(cadd(cadd(cscale(g[0], X1), cscale(g[1], X2)), cscale(g[2], X3)), -1.0);
@@ -590,10 +603,10 @@ __device__ void process_pair(const OrderTables *__restrict__ tab, const PairItem
             const cd F1 = cadd(cscale(hn[0], W0), csub(cscale(hn[2], W2), cscale(hn[1], W3)));
             const cd F2 = cadd(cscale(hn[1], W0), csub(cscale(hn[0], W3), cscale(hn[2], W1)));
             const cd F3 = cadd(cscale(hn[2], W0), csub(cscale(hn[1], W1), cscale(hn[0], W2)));
-            Bds[4 * lm] = f * (dI0.y + E0.y + F0.y);
-            Bds[4 * lm + 1] = f * (dI1.y + E1.y + F1.y);
-            Bds[4 * lm + 2] = f * (dI2.y + E2.y + F2.y);
-            Bds[4 * lm + 3] = f * (dI3.y + E3.y + F3.y);
+            Bds[4 * lm] = f * (dI0 + E0.y + F0.y);
+            Bds[4 * lm + 1] = f * (dI1 + E1.y + F1.y);
+            Bds[4 * lm + 2] = f * (dI2 + E2.y + F2.y);
+            Bds[4 * lm + 3] = f * (dI3 + E3.y + F3.y);
         }
     }
     __syncwarp();
