@@ -456,9 +456,11 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
             }
         }
         __syncthreads();
-        // L: translations and I[gamma], one thread per (pair, (l, m))
+        // L: translations and I[gamma], one thread per (pair, (l, m)); items ordered with
+        // the largest l first and the pair index fastest, so that the lanes of a warp
+        // run loops of similar length
         for (int f = tid; f < nt * NP; f += nth) {
-            const int pl = f / NP, lm = f % NP;
+            const int pl = f % nt, lm = NP - 1 - f / nt;
             double *sw = SW(pl);
             const double *nut = sw + Z::NUT, *Om = sw + Z::OM;
             const cd *St = reinterpret_cast<const cd *>(sw + Z::ST), *gSt = reinterpret_cast<const cd *>(sw + Z::GST);
