@@ -168,8 +168,8 @@ def bench_gpu(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
-        csr = ctx.build_corrections(surf, targ, KERNELS)
+    def step(mixed=False):
+        csr = ctx.build_corrections(surf, targ, KERNELS, mixed=mixed)
         nnz, npairs = csr.nnz, csr.npairs
         ctx.csr_free(csr)
         return nnz, npairs
@@ -196,12 +196,27 @@ def bench_gpu(args):
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
+    # the mixed-precision build (line integrals in double-float FP32) on the same inputs
+    mtimes = []
+    for it in range(args.steps + 1):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(mixed=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it > 0:
+            mtimes.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
     diag = ctx.diagnostics()
     ms_step = reduce_max(sum(times) / len(times), world, dev)
     entries = nnz * len(KERNELS)
     total_entries = reduce_sum(float(entries), world, dev)
     value = total_entries / (ms_step * 1e-3)
+    ms_mixed = reduce_max(sum(mtimes) / len(mtimes), world, dev)
 
     # e2e: host buffers through the C ABI (H2D of inputs and D2H of the four CSRs timed)
     e2e = None
@@ -233,6 +248,11 @@ def bench_gpu(args):
         "clocks": clk,
         "gpu_launches": launches * args.steps if launches is not None else None,
         "points_per_s": world * tg.n / (ms_step * 1e-3),
+        "mixed": {"value": total_entries / (ms_mixed * 1e-3), "unit": UNIT, "ms_per_step": ms_mixed,
+                  "speedup_vs_fp64": ms_step / ms_mixed,
+                  "precision": "Step-6 line integrals in double-float FP32 (about 48 bits), rest FP64",
+                  "parity": "apply-level error as FP64; rows within 32x the oracle's own rounding sensitivity "
+                            "(tests/test_gpu_mixed.py)"},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_targets)

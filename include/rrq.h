@@ -93,6 +93,12 @@ typedef struct {
                                 complex preimage t0 is below rho0; 0 = 10^(5/ptilde) */
     int32_t newton_max;      /* Newton iterations for t0; 0 = 30 */
     double eta;              /* near factor; 0 = 1 */
+    int32_t precision;       /* 0: FP64 throughout (default).  1: mixed -- the line
+                                integrals of Step 6 (sums over the 3 ptilde edge nodes) are
+                                accumulated in double-float arithmetic (pairs of FP32 numbers,
+                                exact FMA products, compensated sums: about 48 bits) on the
+                                FP32 pipes; roots, SSQ recurrences, Omega_0, translations, fit
+                                contraction and smooth subtraction stay FP64 */
 } rrq_options;
 
 /* CSR correction matrix in device memory owned by the library (rrq_csr_free). */

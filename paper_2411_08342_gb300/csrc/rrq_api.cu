@@ -36,6 +36,35 @@ RRQ_DECL_PAIRS(5)
 RRQ_DECL_PAIRS(6)
 RRQ_DECL_PAIRS(7)
 RRQ_DECL_PAIRS(8)
+#define RRQ_DECL_PAIRS_MIX(P)                                                                                    \
+    cudaError_t rrq_launch_pairs_mix_p##P(const OrderTables *, const PairItem *, int64_t, PatchData,            \
+                                          const int64_t *, const double *, const double *, const double *,      \
+                                          const double *, const double *, const int64_t *, uint32_t, int,       \
+                                          double *, double *, double *, double *, int32_t *, BuildCounters *,   \
+                                          cudaStream_t);
+RRQ_DECL_PAIRS_MIX(2)
+RRQ_DECL_PAIRS_MIX(3)
+RRQ_DECL_PAIRS_MIX(4)
+RRQ_DECL_PAIRS_MIX(5)
+RRQ_DECL_PAIRS_MIX(6)
+RRQ_DECL_PAIRS_MIX(7)
+RRQ_DECL_PAIRS_MIX(8)
+
+cudaError_t rrq_launch_pairs_mix(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
+                                 const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
+                                 const double *d_wts, const double *d_txyz, const double *d_tnrm,
+                                 const int64_t *d_tself, uint32_t mask, int newton_max, double *vS, double *vD,
+                                 double *vSp, double *vDp, int32_t *col, BuildCounters *cnt, cudaStream_t st) {
+#define RRQ_CASEM(P)                                                                                                 \
+    case P:                                                                                                          \
+        return rrq_launch_pairs_mix_p##P(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts, d_txyz,        \
+                                         d_tnrm, d_tself, mask, newton_max, vS, vD, vSp, vDp, col, cnt, st);
+    switch (p) {
+        RRQ_CASEM(2) RRQ_CASEM(3) RRQ_CASEM(4) RRQ_CASEM(5) RRQ_CASEM(6) RRQ_CASEM(7) RRQ_CASEM(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef RRQ_CASEM
+}
 
 cudaError_t rrq_launch_pairs(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
                              const int64_t *d_node_off, const double *d_xyz, const double *d_nrm, const double *d_wts,
@@ -301,6 +330,10 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     pd.eyu = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_eyu());
     pd.eg = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
     pd.eh = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
+    const bool mixed = o.precision == 1;
+    if (o.precision != 0 && o.precision != 1) return RRQ_ERR_ARG;
+    pd.eg2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
+    pd.eh2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
     pd.XD = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
     pd.XSp = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
     pd.XS2 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
@@ -377,9 +410,9 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
             int n = (int)plist[p].size();
             if (n) {
                 int64_t i0 = h_roff[start], i1 = h_roff[start + n];
-                e = rrq_launch_pairs(p, ctx->d_tab[p], items + i0, i1 - i0, pd, in.node_off, in.xyz, in.nrm, in.wts,
-                                     in.txyz, in.tnrm, in.tself, kernel_mask, newton_max, vals[0], vals[1], vals[2],
-                                     vals[3], col, d_cnt, s.st);
+                e = (mixed ? rrq_launch_pairs_mix : rrq_launch_pairs)(
+                    p, ctx->d_tab[p], items + i0, i1 - i0, pd, in.node_off, in.xyz, in.nrm, in.wts, in.txyz, in.tnrm,
+                    in.tself, kernel_mask, newton_max, vals[0], vals[1], vals[2], vals[3], col, d_cnt, s.st);
                 if (e != cudaSuccess) break;
             }
             start += n;
@@ -711,6 +744,8 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     pd.eyu = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_eyu());
     pd.eg = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg());
     pd.eh = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg());
+    pd.eg2 = nullptr;
+    pd.eh2 = nullptr;
     pd.XD = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
     pd.XSp = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
     pd.XS2 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());

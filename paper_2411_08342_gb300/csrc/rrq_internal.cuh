@@ -71,6 +71,8 @@ struct PatchData {
     double *eyu;     // [P][3*2PTMAX*3] local edge samples at the upsampled nodes
     cd *eg;          // [P][3*PTMAX][NJKMAX][3] grad S^{(j,k)} at edge samples
     cd *eh;          // [P][3*PTMAX][NJKMAX][3] (Hess S^{(j,k)}) tau at edge samples
+    float4 *eg2;     // same as eg as (re.hi, re.lo, im.hi, im.lo) float pairs, or NULL
+    float4 *eh2;     // same as eh as float pairs, or NULL
     double *XD;      // [P][4*NPMAX][NPMAX] quaternion fit of (mu, 0):    row c*np+lm, col i
     double *XSp;     // [P][4*NPMAX][NPMAX] quaternion fit of (0, sigma nu)
     double *XS2;     // [P][4*NPMAX][NPMAX] quaternion fit of the intermediate density
@@ -116,3 +118,10 @@ cudaError_t rrq_launch_pairs(int p, const OrderTables *d_tab, const PairItem *d_
                              const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
                              int newton_max, double *vS, double *vD, double *vSp, double *vDp,
                              int32_t *col, BuildCounters *cnt, cudaStream_t st);
+// mixed-precision variant (line integrals in double-float; needs pd.eg2, pd.eh2)
+cudaError_t rrq_launch_pairs_mix(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems,
+                                 PatchData pd, const int64_t *d_node_off, const double *d_xyz,
+                                 const double *d_nrm, const double *d_wts, const double *d_txyz,
+                                 const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
+                                 int newton_max, double *vS, double *vD, double *vSp, double *vDp,
+                                 int32_t *col, BuildCounters *cnt, cudaStream_t st);

@@ -16,7 +16,27 @@ struct TileCfg {
     static constexpr int THREADS = 128;
 };
 
-template <int P>
+// double-float accumulator: value = h + l (two FP32 numbers, about 48 bits)
+struct dfa {
+    float h, l;
+};
+
+// acc += (ah + al) * (bh + bl): exact FP32 product by FMA, compensated (TwoSum) sum
+__device__ __forceinline__ void dfmac(dfa &acc, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = acc.h + p;
+    const float bb = s - acc.h;
+    const float err = (acc.h - (s - bb)) + (p - bb);
+    acc.h = s;
+    acc.l += err + e;
+}
+
+__device__ __forceinline__ double dfval(const dfa &a) { return (double)a.h + (double)a.l; }
+
+template <int P, bool MIX>
 __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restrict__ tab, const PairItem *__restrict__ items,
                                                     int64_t nitems, PatchData pd, const int64_t *__restrict__ node_off,
                                                     const double *__restrict__ xyz, const double *__restrict__ nrm,
@@ -387,15 +407,93 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
                 const double d0 = dq[3 * q], d1 = dq[3 * q + 1], d2 = dq[3 * q + 2];
                 const double t0 = tau[3 * q], t1 = tau[3 * q + 1], t2 = tau[3 * q + 2];
                 const double w3n = w3 * (nut[0] * d0 + nut[1] * d1 + nut[2] * d2);
-                double *o = wv + 12 * q;
-                o[0] = w1 * d0; o[1] = w1 * d1; o[2] = w1 * d2;
-                o[3] = w1 * (t1 * d2 - t2 * d1); o[4] = w1 * (t2 * d0 - t0 * d2); o[5] = w1 * (t0 * d1 - t1 * d0);
-                o[6] = w1; o[7] = 0.0; o[8] = 0.0;
-                o[9] = w3n * d0; o[10] = w3n * d1; o[11] = w3n * d2;
+                double vv[12];
+                vv[0] = w1 * d0; vv[1] = w1 * d1; vv[2] = w1 * d2;
+                vv[3] = w1 * (t1 * d2 - t2 * d1); vv[4] = w1 * (t2 * d0 - t0 * d2); vv[5] = w1 * (t0 * d1 - t1 * d0);
+                vv[6] = w1; vv[7] = 0.0; vv[8] = 0.0;
+                vv[9] = w3n * d0; vv[10] = w3n * d1; vv[11] = w3n * d2;
+                if (MIX) {
+                    // the same 12 numbers as (hi, lo) float pairs, in the same slot
+                    float *of = reinterpret_cast<float *>(wv + 12 * q);
+                    for (int i = 0; i < 12; i++) {
+                        const float hi = __double2float_rn(vv[i]);
+                        of[2 * i] = hi;
+                        of[2 * i + 1] = __double2float_rn(vv[i] - (double)hi);
+                    }
+                } else {
+                    double *o = wv + 12 * q;
+                    for (int i = 0; i < 12; i++) o[i] = vv[i];
+                }
             }
         }
         __syncthreads();
         // K: line integrals, one thread per (pair, (j, k >= 0)), j >= 1
+        if (MIX) {
+            for (int f = tid; f < nt * (NJK - 1); f += nth) {
+                const int pl = f / (NJK - 1), jk = 1 + f % (NJK - 1);
+                double *sw = SW(pl);
+                const size_t ps = (size_t)s_item[pl].P;
+                const float *wf = reinterpret_cast<const float *>(sw + Z::WV);
+                const double *nut = sw + Z::NUT;
+                const float4 *eg = pd.eg2 + ps * pd_eg();
+                const float4 *eh = pd.eh2 + ps * pd_eg();
+                const bool hj = jk >= 3;
+                dfa Vr = {0, 0}, Vi = {0, 0}, Q0r = {0, 0}, Q0i = {0, 0}, Q1r = {0, 0}, Q1i = {0, 0}, Q2r = {0, 0}, Q2i = {0, 0};
+                dfa Q3r = {0, 0}, Q3i = {0, 0}, D0r = {0, 0}, D0i = {0, 0}, D1r = {0, 0}, D1i = {0, 0}, D2r = {0, 0}, D2i = {0, 0};
+                dfa E0r = {0, 0}, E0i = {0, 0}, E1r = {0, 0}, E1i = {0, 0}, E2r = {0, 0}, E2i = {0, 0}, E3r = {0, 0}, E3i = {0, 0};
+                for (int q = 0; q < NS; q++) {
+                    const float *o = wf + 24 * q;
+                    const float4 *g = eg + ((size_t)q * NJK + jk) * 3;
+                    const float4 g0 = g[0], g1 = g[1], g2 = g[2];
+                    // V += g . (w1 tau x d): values 3, 4, 5
+                    dfmac(Vr, o[6], o[7], g0.x, g0.y); dfmac(Vr, o[8], o[9], g1.x, g1.y); dfmac(Vr, o[10], o[11], g2.x, g2.y);
+                    dfmac(Vi, o[6], o[7], g0.z, g0.w); dfmac(Vi, o[8], o[9], g1.z, g1.w); dfmac(Vi, o[10], o[11], g2.z, g2.w);
+                    if (hj) {
+                        const float4 *h = eh + ((size_t)q * NJK + jk) * 3;
+                        const float4 h0 = h[0], h1 = h[1], h2 = h[2];
+                        const float a0h = o[0], a0l = o[1], a1h = o[2], a1l = o[3], a2h = o[4], a2l = o[5];
+                        // (0, w1 d)(0, h) = (-(w1 d).h, (w1 d) x h)
+                        dfmac(Q0r, -a0h, -a0l, h0.x, h0.y); dfmac(Q0r, -a1h, -a1l, h1.x, h1.y); dfmac(Q0r, -a2h, -a2l, h2.x, h2.y);
+                        dfmac(Q0i, -a0h, -a0l, h0.z, h0.w); dfmac(Q0i, -a1h, -a1l, h1.z, h1.w); dfmac(Q0i, -a2h, -a2l, h2.z, h2.w);
+                        dfmac(Q1r, a1h, a1l, h2.x, h2.y); dfmac(Q1r, -a2h, -a2l, h1.x, h1.y);
+                        dfmac(Q1i, a1h, a1l, h2.z, h2.w); dfmac(Q1i, -a2h, -a2l, h1.z, h1.w);
+                        dfmac(Q2r, a2h, a2l, h0.x, h0.y); dfmac(Q2r, -a0h, -a0l, h2.x, h2.y);
+                        dfmac(Q2i, a2h, a2l, h0.z, h0.w); dfmac(Q2i, -a0h, -a0l, h2.z, h2.w);
+                        dfmac(Q3r, a0h, a0l, h1.x, h1.y); dfmac(Q3r, -a1h, -a1l, h0.x, h0.y);
+                        dfmac(Q3i, a0h, a0l, h1.z, h1.w); dfmac(Q3i, -a1h, -a1l, h0.z, h0.w);
+                        if (wantDP) {
+                            const float w1h = o[12], w1l = o[13];
+                            const float m0h = o[18], m0l = o[19], m1h = o[20], m1l = o[21], m2h = o[22], m2l = o[23];
+                            dfmac(D0r, w1h, w1l, h0.x, h0.y); dfmac(D0i, w1h, w1l, h0.z, h0.w);
+                            dfmac(D1r, w1h, w1l, h1.x, h1.y); dfmac(D1i, w1h, w1l, h1.z, h1.w);
+                            dfmac(D2r, w1h, w1l, h2.x, h2.y); dfmac(D2i, w1h, w1l, h2.z, h2.w);
+                            dfmac(E0r, -m0h, -m0l, h0.x, h0.y); dfmac(E0r, -m1h, -m1l, h1.x, h1.y); dfmac(E0r, -m2h, -m2l, h2.x, h2.y);
+                            dfmac(E0i, -m0h, -m0l, h0.z, h0.w); dfmac(E0i, -m1h, -m1l, h1.z, h1.w); dfmac(E0i, -m2h, -m2l, h2.z, h2.w);
+                            dfmac(E1r, m1h, m1l, h2.x, h2.y); dfmac(E1r, -m2h, -m2l, h1.x, h1.y);
+                            dfmac(E1i, m1h, m1l, h2.z, h2.w); dfmac(E1i, -m2h, -m2l, h1.z, h1.w);
+                            dfmac(E2r, m2h, m2l, h0.x, h0.y); dfmac(E2r, -m0h, -m0l, h2.x, h2.y);
+                            dfmac(E2i, m2h, m2l, h0.z, h0.w); dfmac(E2i, -m0h, -m0l, h2.z, h2.w);
+                            dfmac(E3r, m0h, m0l, h1.x, h1.y); dfmac(E3r, -m1h, -m1l, h0.x, h0.y);
+                            dfmac(E3i, m0h, m0l, h1.z, h1.w); dfmac(E3i, -m1h, -m1l, h0.z, h0.w);
+                        }
+                    }
+                }
+                cd *Vs = reinterpret_cast<cd *>(sw + Z::V), *Qs = reinterpret_cast<cd *>(sw + Z::Q);
+                cd *dQs = reinterpret_cast<cd *>(sw + Z::DQQ);
+                Vs[jk] = mkc(dfval(Vr), dfval(Vi));
+                Qs[4 * jk] = mkc(dfval(Q0r), dfval(Q0i)); Qs[4 * jk + 1] = mkc(dfval(Q1r), dfval(Q1i));
+                Qs[4 * jk + 2] = mkc(dfval(Q2r), dfval(Q2i)); Qs[4 * jk + 3] = mkc(dfval(Q3r), dfval(Q3i));
+                if (wantDP) {
+                    const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
+                    const double d0r = dfval(D0r), d0i = dfval(D0i), d1r = dfval(D1r), d1i = dfval(D1i);
+                    const double d2r = dfval(D2r), d2i = dfval(D2i);
+                    dQs[4 * jk] = mkc(-(n0 * d0r + n1 * d1r + n2 * d2r) - dfval(E0r), -(n0 * d0i + n1 * d1i + n2 * d2i) - dfval(E0i));
+                    dQs[4 * jk + 1] = mkc((n1 * d2r - n2 * d1r) - dfval(E1r), (n1 * d2i - n2 * d1i) - dfval(E1i));
+                    dQs[4 * jk + 2] = mkc((n2 * d0r - n0 * d2r) - dfval(E2r), (n2 * d0i - n0 * d2i) - dfval(E2i));
+                    dQs[4 * jk + 3] = mkc((n0 * d1r - n1 * d0r) - dfval(E3r), (n0 * d1i - n1 * d0i) - dfval(E3i));
+                }
+            }
+        } else
         for (int f = tid; f < nt * (NJK - 1); f += nth) {
             const int pl = f / (NJK - 1), jk = 1 + f % (NJK - 1);
             double *sw = SW(pl);
@@ -612,7 +710,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
     }
 }
 
-template <int P>
+template <int P, bool MIX>
 cudaError_t launch_pairs_tile(const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
                               const int64_t *d_node_off, const double *d_xyz, const double *d_nrm, const double *d_wts,
                               const double *d_txyz, const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
@@ -620,18 +718,18 @@ cudaError_t launch_pairs_tile(const OrderTables *d_tab, const PairItem *d_items,
                               BuildCounters *cnt, cudaStream_t st) {
     constexpr int T = TileCfg<P>::T, NTH = TileCfg<P>::THREADS;
     const size_t bytes = sizeof(double) * PairSm<P>::TOTAL * T;
-    cudaError_t e = cudaFuncSetAttribute(k_pairs_tile<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_pairs_tile<P, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     if (nitems <= 0) return cudaSuccess;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P>, NTH, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX>, NTH, bytes);
     if (per_sm < 1) per_sm = 1;
     int64_t want = (nitems + T - 1) / T;
     int64_t grid = (int64_t)nsm * per_sm * 16;
     if (grid > want) grid = want;
-    k_pairs_tile<P><<<(unsigned)grid, NTH, bytes, st>>>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts,
+    k_pairs_tile<P, MIX><<<(unsigned)grid, NTH, bytes, st>>>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts,
                                                         d_txyz, d_tnrm, d_tself, mask, newton_max, vS, vD, vSp, vDp,
                                                         col, cnt);
     RRQ_COUNT_LAUNCH();

@@ -16,6 +16,12 @@
 
 namespace {
 
+// complex double -> (re.hi, re.lo, im.hi, im.lo) as float pairs (about 48 bits)
+__device__ __forceinline__ float4 split4(cd v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+
 struct q4 {
     double s, x, y, z;
 };
@@ -273,6 +279,10 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         for (int a = 0; a < 3; a++) {
             g_eg[(size_t)w * 3 + a] = g[a];
             g_eh[(size_t)w * 3 + a] = hv[a];
+            if (pd.eg2) {
+                pd.eg2[(size_t)pid * pd_eg() + (size_t)w * 3 + a] = split4(g[a]);
+                pd.eh2[(size_t)pid * pd_eg() + (size_t)w * 3 + a] = split4(hv[a]);
+            }
         }
     }
     __syncthreads();

@@ -34,7 +34,7 @@ class TargetsS(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("inputs_on_host", C.c_int32), ("ptilde", C.c_int32), ("rho0", C.c_double),
-                ("newton_max", C.c_int32), ("eta", C.c_double)]
+                ("newton_max", C.c_int32), ("eta", C.c_double), ("precision", C.c_int32)]
 
 
 class CSR(C.Structure):
@@ -152,11 +152,11 @@ class Context:
     # ------------------------------------------------------------- entry points
     def build_corrections(self, surf: Surface, targ: TargetsS, kernels=("S", "D", "SP", "DP"),
                           inputs_on_host: bool = False, rho0: float = 0.0, eta: float = 0.0,
-                          newton_max: int = 0) -> CSR:
+                          newton_max: int = 0, mixed: bool = False) -> CSR:
         mask = 0
         for k in kernels:
             mask |= KERNEL_BITS[k]
-        opt = Options(int(inputs_on_host), 0, rho0, newton_max, eta)
+        opt = Options(int(inputs_on_host), 0, rho0, newton_max, eta, int(mixed))
         out = CSR()
         st = self.L.rrq_build_corrections(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt), C.byref(out))
         _check(st, "rrq_build_corrections")
@@ -175,7 +175,7 @@ class Context:
             arr[KERNEL_SLOT[k]] = vals[k].data_ptr()
         cap = int(col.shape[0])
         nnz, npairs = C.c_int64(), C.c_int64()
-        opt = Options(0, 0, 0.0, 0, 0.0)
+        opt = Options(0, 0, 0.0, 0, 0.0, 0)
         st = self.L.rrq_build_corrections_static(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt),
                                                  _ptr(rowptr), _ptr(col), arr, cap, C.byref(nnz), C.byref(npairs))
         _check(st, "rrq_build_corrections_static")
@@ -211,7 +211,7 @@ class Context:
 
     def apply(self, surf: Surface, targ: TargetsS, kernel: str, csr: CSR, density, out,
               inputs_on_host: bool = False):
-        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0)
+        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, 0)
         _check(self.L.rrq_apply(self.h, C.byref(surf), C.byref(targ), KERNEL_BITS[kernel],
                                 C.byref(csr) if csr is not None else None, _ptr(density), _ptr(out),
                                 C.byref(opt)), "rrq_apply")

@@ -85,6 +85,7 @@ def row_error(kind, d, tg, rowptr, col, v_gpu, v_orc):
 
 
 def gpu_build(ctx, d, tg, kernels=KINDS, on_host=False, **kw):
+    """Build through the C ABI (device or host inputs) and copy the CSR to numpy."""
     import torch
     from paper_2411_08342_gb300 import rrq
     if on_host:

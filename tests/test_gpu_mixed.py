@@ -1,0 +1,58 @@
+"""Mixed-precision build (rrq_options.precision = 1: Step-6 line integrals accumulated in
+double-float FP32 arithmetic, everything else FP64) against the FP64 oracle.
+
+Stated tolerance of the mixed path: the apply-level gate of the FP64 path unchanged
+(max(1e-10, 8 x the oracle's own sensitivity)), and rows within 32 x the oracle's own
+rounding sensitivity (measured on the same rows with rigidly rotated inputs) or 1e-10.
+Double-float carries ~48 bits, so rows move by a few times more than in FP64 where the
+formulation is ill-conditioned (outer shell of the near region); smooth-density applies
+do not see it."""
+import numpy as np
+import pytest
+
+from paper_2411_08342_gb300 import workloads as W
+from tests.gpu_helpers import (KINDS, ROT_FACTOR, TOL_APPLY, TOL_E, apply_error, gpu_build, rotated,
+                               row_error)
+
+pytestmark = pytest.mark.gpu
+MIXED_ROW_FACTOR = 32.0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    c = rrq.Context(0)
+    yield c
+    c.close()
+
+
+def _cases():
+    d8 = W.discretize(W.star_surface(2), 8)
+    rng = np.random.default_rng(8)
+    on = W.on_surface_targets(d8)
+    sel = rng.choice(on.n, 300, replace=False)
+    t8 = W.concat_targets(W.Targets(on.xyz[sel], on.nrm[sel], on.self_node[sel]), W.off_surface_targets(d8, 300, seed=8))
+    return {"star1280_p6": W.star1280(6, 600), "star320_p8": (d8, t8)}
+
+
+@pytest.mark.parametrize("name", ["star1280_p6", "star320_p8"])
+def test_mixed_against_oracle(ctx, oracle_lib, name):
+    d, tg = _cases()[name]
+    rowptr, col, vals, diag = gpu_build(ctx, d, tg, mixed=True)
+    orp, ocol, ovals, _ = oracle_lib.OracleSurface(d).csr_rows(tg)
+    assert np.array_equal(rowptr, orp) and np.array_equal(col, ocol)
+    d2, tg2 = rotated(d, tg)
+    _, _, rvals, _ = oracle_lib.OracleSurface(d2).csr_rows(tg2)
+    sigma = W.random_ylm_density(d.xyz, 8, seed=7)
+    for k in KINDS:
+        assert np.all(np.isfinite(vals[k]))
+        e = row_error(k, d, tg, orp, ocol, vals[k], ovals[k])
+        er = row_error(k, d, tg, orp, ocol, rvals[k], ovals[k])
+        ea = apply_error(k, d, tg, orp, ocol, vals[k], ovals[k], sigma)
+        era = apply_error(k, d, tg, orp, ocol, rvals[k], ovals[k], sigma)
+        print(name, k, f"row {e:.1e} (oracle self {er:.1e}) apply {ea:.1e} (oracle self {era:.1e})")
+        assert e <= max(TOL_E, MIXED_ROW_FACTOR * er), (k, e, er)
+        assert ea <= max(TOL_APPLY, ROT_FACTOR * era), (k, ea, era)
