@@ -404,14 +404,25 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
             if (vals[k]) cudaFreeAsync(vals[k], s.st);
         return RRQ_ERR_OOM;
     }
+    EdgeRoot *roots = (EdgeRoot *)Scratch::alloc(&s, sizeof(EdgeRoot) * 3 * (nb.npairs > 0 ? nb.npairs : 1));
+    if (!roots) oom = true;
+    if (oom) {
+        cudaFreeAsync(d_rowptr, s.st);
+        cudaFreeAsync(col, s.st);
+        for (int k = 0; k < 4; k++)
+            if (vals[k]) cudaFreeAsync(vals[k], s.st);
+        return RRQ_ERR_OOM;
+    }
     {
         int start = 0;
         for (int p = 2; p <= RRQ_PMAX; p++) {
             int n = (int)plist[p].size();
             if (n) {
                 int64_t i0 = h_roff[start], i1 = h_roff[start + n];
+                PatchData pdo = pd;
+                pdo.roots = roots + 3 * i0;
                 e = (mixed ? rrq_launch_pairs_mix : rrq_launch_pairs)(
-                    p, ctx->d_tab[p], items + i0, i1 - i0, pd, in.node_off, in.xyz, in.nrm, in.wts, in.txyz, in.tnrm,
+                    p, ctx->d_tab[p], items + i0, i1 - i0, pdo, in.node_off, in.xyz, in.nrm, in.wts, in.txyz, in.tnrm,
                     in.tself, kernel_mask, newton_max, vals[0], vals[1], vals[2], vals[3], col, d_cnt, s.st);
                 if (e != cudaSuccess) break;
             }
@@ -805,13 +816,21 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
                  (long long)nnz, (long long)capacity);
         return RRQ_ERR_ARG;
     }
+    pd.roots = (EdgeRoot *)StaticArena::alloc(&ar, sizeof(EdgeRoot) * 3 * (nb.npairs > 0 ? nb.npairs : 1));
+    if (ar.failed) {
+        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
+                 ar.wanted, (size_t)RRQ_STATIC_SCRATCH_BYTES);
+        return RRQ_ERR_ARG;
+    }
     {
         int start = 0;
         for (int p = 2; p <= RRQ_PMAX; p++) {
             int n = (int)plist[p].size();
             if (n) {
                 int64_t i0 = h_roff[start], i1 = h_roff[start + n];
-                CK(rrq_launch_pairs(p, tabs[p], items + i0, i1 - i0, pd, surf->node_off, surf->xyz, surf->nrm,
+                PatchData pdo = pd;
+                pdo.roots = pd.roots + 3 * i0;
+                CK(rrq_launch_pairs(p, tabs[p], items + i0, i1 - i0, pdo, surf->node_off, surf->xyz, surf->nrm,
                                     surf->wts, targ->xyz, targ->nrm, targ->self_node, kernel_mask, newton_max,
                                     (kernel_mask & RRQ_S) ? val[0] : nullptr, (kernel_mask & RRQ_D) ? val[1] : nullptr,
                                     (kernel_mask & RRQ_SP) ? val[2] : nullptr,

@@ -58,6 +58,11 @@ struct OrderTables {
     double L2M[RRQ_PMAX * RRQ_PMAX];                // [n][k] coefficient of t^k in P_n(t)
 };
 
+// Complex preimage of one (pair, edge): Re t0, Im t0, converged (0/1), singularity swap (0/1).
+struct EdgeRoot {
+    double x, y, z, w;
+};
+
 // Device-side per-patch data (strides sized for the largest order of the surface).
 struct PatchData {
     int npatch;
@@ -78,6 +83,7 @@ struct PatchData {
     double *XS2;     // [P][4*NPMAX][NPMAX] quaternion fit of the intermediate density
     double *XS1;     // [P][NPMAX][NPMAX]   scalar fit A_S^{-1}
     int *status;     // [P] 0 ok, nonzero = singular fit / degenerate patch
+    EdgeRoot *roots;  // [pair item][3 edges]: (Re t0, Im t0, converged, singularity swap)
 };
 
 static const size_t PD_FRAME = 16, PD_BOUNDS = 5;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
                 double *dq = sw + Z::DQ, *tau = sw + Z::TAU;
                 dq[3 * q] = d0; dq[3 * q + 1] = d1; dq[3 * q + 2] = d2;
                 tau[3 * q] = et[0]; tau[3 * q + 1] = et[1]; tau[3 * q + 2] = et[2];
-                sw[Z::RINV + q] = 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                sw[Z::RINV + q] = rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
             } else {
                 target_table<P>(yt, reinterpret_cast<cd *>(sw + Z::ST), it - NS);
             }
@@ -164,19 +164,19 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
             const double *yt = sw + Z::YT, *dq = sw + Z::DQ;
             double mplus = 2.0, mminus = 2.0;
             for (int s2 = lane; s2 < NP + NS; s2 += 32) {
-                double dz, dl;
+                double dz, dl2;
                 if (s2 < NP) {
                     const double *yn = pd.ynode + ps * pd_ynode() + 3 * s2;
                     const double d0 = yt[0] - yn[0], d1 = yt[1] - yn[1];
                     dz = yt[2] - yn[2];
-                    dl = sqrt(d0 * d0 + d1 * d1 + dz * dz);
+                    dl2 = d0 * d0 + d1 * d1 + dz * dz;
                 } else {
                     const int q = s2 - NP;
                     dz = dq[3 * q + 2];
-                    dl = sqrt(dq[3 * q] * dq[3 * q] + dq[3 * q + 1] * dq[3 * q + 1] + dz * dz);
+                    dl2 = dq[3 * q] * dq[3 * q] + dq[3 * q + 1] * dq[3 * q + 1] + dz * dz;
                 }
-                if (dl != 0.0) {
-                    const double cz = dz / dl;
+                if (dl2 != 0.0) {
+                    const double cz = dz * rsqrt(dl2);
                     mplus = fmin(mplus, cz);
                     mminus = fmin(mminus, -cz);
                 }
@@ -189,67 +189,22 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
                 if ((uz > 0 ? mplus : mminus) < -0.5) atomicAdd(&bc[2], 1u);
             }
         }
-        // F: roots and moments, one thread per (pair, edge)
+        // F: complex roots (from k_roots) and singularity-swap moments, one thread per (pair, edge)
         for (int f = tid; f < nt * 3; f += nth) {
             const int pl = f / 3, e = f % 3;
             double *sw = SW(pl);
-            const double *yt = sw + Z::YT;
-            const double *ce = sw + Z::EA + 3 * P * e;
-            double ym[3], yp[3];
-            for (int a = 0; a < 3; a++) {
-                double sp = 0, sm = 0;
-                for (int n = 0; n < P; n++) {
-                    sp += ce[3 * n + a];
-                    sm += ((n & 1) ? -1.0 : 1.0) * ce[3 * n + a];
-                }
-                yp[a] = sp;
-                ym[a] = sm;
-            }
-            double c[3], b[3], w[3];
-            for (int a = 0; a < 3; a++) { c[a] = 0.5 * (yp[a] + ym[a]); b[a] = 0.5 * (yp[a] - ym[a]); w[a] = yt[a] - c[a]; }
-            const double bw0 = b[1] * w[2] - b[2] * w[1], bw1 = b[2] * w[0] - b[0] * w[2], bw2 = b[0] * w[1] - b[1] * w[0];
-            const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-            cd tt = mkc((b[0] * w[0] + b[1] * w[1] + b[2] * w[2]) / bb, sqrt(bw0 * bw0 + bw1 * bw1 + bw2 * bw2) / bb);
-            int conv = 0;
-            bool skip = false;
-            {
-                const cd zm1 = mkc(tt.x - 1.0, tt.y), zp1 = mkc(tt.x + 1.0, tt.y);
-                const cd wv = cadd(tt, cmul(sqrt_c(zm1), sqrt_c(zp1)));
-                double rc = sqrt(cabs2(wv));
-                if (rc < 1.0) rc = 1.0 / rc;
-                if (rc > 1.5 * tab->rho0 && tt.y > 0.0) { skip = true; conv = 1; }
-            }
-            for (int it = 0; it < (skip ? 0 : newton_max); it++) {
-                cd y[3], dy[3];
-                edge_eval_cplx(ce, P, tt, y, dy);
-                cd g = mkc(0, 0), gp = mkc(0, 0);
-                for (int a = 0; a < 3; a++) {
-                    const cd r = mkc(y[a].x - yt[a], y[a].y);
-                    g = cadd(g, cmul(r, r));
-                    gp = cadd(gp, cscale(cmul(r, dy[a]), 2.0));
-                }
-                if (gp.x == 0.0 && gp.y == 0.0) break;
-                const cd dt = cdivz(g, gp);
-                tt = csub(tt, dt);
-                const double at = sqrt(cabs2(tt));
-                if (sqrt(cabs2(dt)) <= 1e-14 * (at > 1.0 ? at : 1.0)) { conv = 1; break; }
-            }
-            if (tt.y < 0) tt.y = -tt.y;
-            const cd zm1 = mkc(tt.x - 1.0, tt.y), zp1 = mkc(tt.x + 1.0, tt.y);
-            const cd wv = cadd(tt, cmul(sqrt_c(zm1), sqrt_c(zp1)));
-            double rho = sqrt(cabs2(wv));
-            if (rho < 1.0) rho = 1.0 / rho;
-            const int ssq = conv && rho < tab->rho0 && tt.y > 0.0;
+            const EdgeRoot rt = pd.roots[(base + pl) * 3 + e];
+            const int conv = rt.z != 0.0, ssq = rt.w != 0.0;
             double *t0s = sw + Z::T0;
-            t0s[4 * e] = tt.x;
-            t0s[4 * e + 1] = tt.y;
-            t0s[4 * e + 2] = conv;
-            t0s[4 * e + 3] = ssq;
+            t0s[4 * e] = rt.x;
+            t0s[4 * e + 1] = rt.y;
+            t0s[4 * e + 2] = rt.z;
+            t0s[4 * e + 3] = rt.w;
             if (!conv) atomicAdd(&bc[0], 1u);
-            if (conv && tt.y < 1e-14 && fabs(tt.x) <= 1.0) atomicAdd(&bc[1], 1u);
+            if (conv && rt.y < 1e-14 && fabs(rt.x) <= 1.0) atomicAdd(&bc[1], 1u);
             atomicAdd(ssq ? &bc[3] : &bc[4], 1u);
             if (ssq) {
-                const double a = tt.x, bi = tt.y, c0 = a * a + bi * bi;
+                const double a = rt.x, bi = rt.y, c0 = a * a + bi * bi;
                 const double sp = sqrt((1 - a) * (1 - a) + bi * bi), sm = sqrt((1 + a) * (1 + a) + bi * bi);
                 double *J = sw + Z::MOM + 2 * NUP * e, *K = J + PT;
                 J[0] = asinh((1 - a) / bi) + asinh((1 + a) / bi);
@@ -710,6 +665,76 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
     }
 }
 
+// Step 5, complex preimage t0 of every (pair, edge): Newton on sum_a (y_a(t) - y'_a)^2
+// from the root of the straight chord (|dt| <= 1e-14 max(1,|t|), newton_max steps), Im t0 >= 0;
+// an edge whose chord root is outside 1.5 rho0 takes the upsampled rule and keeps the chord
+// root.  One thread per (pair, edge), so the Newton chains of many pairs overlap.
+template <int P>
+__global__ void __launch_bounds__(128) k_roots(const OrderTables *__restrict__ tab, const PairItem *__restrict__ items,
+                                               int64_t nitems, PatchData pd, const double *__restrict__ txyz,
+                                               int newton_max) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nitems * 3) return;
+    const int64_t n = idx / 3;
+    const int e = (int)(idx % 3);
+    const PairItem im = items[n];
+    const double *fr = pd.frame + (size_t)im.P * PD_FRAME;
+    double yt[3];
+    for (int b = 0; b < 3; b++) {
+        double sy = 0;
+        for (int a = 0; a < 3; a++) sy += fr[3 + 3 * a + b] * (txyz[3 * im.t + a] - fr[a]);
+        yt[b] = fr[12] * sy;
+    }
+    double ce[3 * P];
+    for (int i = 0; i < 3 * P; i++) ce[i] = pd.ea[(size_t)im.P * pd_ea() + 3 * P * e + i];
+    double ym[3], yp[3];
+    for (int a = 0; a < 3; a++) {
+        double sp = 0, sm = 0;
+        for (int k = 0; k < P; k++) {
+            sp += ce[3 * k + a];
+            sm += ((k & 1) ? -1.0 : 1.0) * ce[3 * k + a];
+        }
+        yp[a] = sp;
+        ym[a] = sm;
+    }
+    double c[3], b[3], w[3];
+    for (int a = 0; a < 3; a++) { c[a] = 0.5 * (yp[a] + ym[a]); b[a] = 0.5 * (yp[a] - ym[a]); w[a] = yt[a] - c[a]; }
+    const double bw0 = b[1] * w[2] - b[2] * w[1], bw1 = b[2] * w[0] - b[0] * w[2], bw2 = b[0] * w[1] - b[1] * w[0];
+    const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    cd tt = mkc((b[0] * w[0] + b[1] * w[1] + b[2] * w[2]) / bb, sqrt(bw0 * bw0 + bw1 * bw1 + bw2 * bw2) / bb);
+    int conv = 0;
+    bool skip = false;
+    {
+        const cd zm1 = mkc(tt.x - 1.0, tt.y), zp1 = mkc(tt.x + 1.0, tt.y);
+        const cd wv = cadd(tt, cmul(sqrt_c(zm1), sqrt_c(zp1)));
+        double rc = sqrt(cabs2(wv));
+        if (rc < 1.0) rc = 1.0 / rc;
+        if (rc > 1.5 * tab->rho0 && tt.y > 0.0) { skip = true; conv = 1; }
+    }
+    for (int it = 0; it < (skip ? 0 : newton_max); it++) {
+        cd y[3], dy[3];
+        edge_eval_cplx(ce, P, tt, y, dy);
+        cd g = mkc(0, 0), gp = mkc(0, 0);
+        for (int a = 0; a < 3; a++) {
+            const cd r = mkc(y[a].x - yt[a], y[a].y);
+            g = cadd(g, cmul(r, r));
+            gp = cadd(gp, cscale(cmul(r, dy[a]), 2.0));
+        }
+        if (gp.x == 0.0 && gp.y == 0.0) break;
+        const cd dt = cdivz(g, gp);
+        tt = csub(tt, dt);
+        const double at2 = cabs2(tt);
+        if (cabs2(dt) <= 1e-28 * (at2 > 1.0 ? at2 : 1.0)) { conv = 1; break; }
+    }
+    if (tt.y < 0) tt.y = -tt.y;
+    const cd zm1 = mkc(tt.x - 1.0, tt.y), zp1 = mkc(tt.x + 1.0, tt.y);
+    const cd wv = cadd(tt, cmul(sqrt_c(zm1), sqrt_c(zp1)));
+    double rho = sqrt(cabs2(wv));
+    if (rho < 1.0) rho = 1.0 / rho;
+    const int ssq = conv && rho < tab->rho0 && tt.y > 0.0;
+    pd.roots[idx] = EdgeRoot{tt.x, tt.y, (double)conv, (double)ssq};
+}
+
 template <int P, bool MIX>
 cudaError_t launch_pairs_tile(const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
                               const int64_t *d_node_off, const double *d_xyz, const double *d_nrm, const double *d_wts,
@@ -726,6 +751,10 @@ cudaError_t launch_pairs_tile(const OrderTables *d_tab, const PairItem *d_items,
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX>, NTH, bytes);
     if (per_sm < 1) per_sm = 1;
+    k_roots<P><<<(unsigned)((nitems * 3 + 127) / 128), 128, 0, st>>>(d_tab, d_items, nitems, pd, d_txyz, newton_max);
+    RRQ_COUNT_LAUNCH();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     int64_t want = (nitems + T - 1) / T;
     int64_t grid = (int64_t)nsm * per_sm * 16;
     if (grid > want) grid = want;
