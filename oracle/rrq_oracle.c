@@ -334,6 +334,8 @@ typedef struct {
     double tom[ORC_NOM], wom[ORC_NOM];            /* GL per Omega_0 panel */
     double *Eint;                                 /* [3*pt][np] node -> edge GL samples */
     double *Vint;                                 /* [3][np] node -> vertices */
+    double *VdLU;                                 /* [np][np] LU of the transposed Dubiner Vandermonde */
+    int *VdPiv;                                   /* its pivots */
 } orc_order;
 
 /* edge e parametrisation (u,v)(t), t in [-1,1]: E0 v0->v1, E1 v1->v2, E2 v2->v0 */
@@ -405,14 +407,19 @@ static int order_init(orc_order *O, int p, const double *ref_uv, const orc_opts 
         for (int i = 0; i < np; i++) O->Eint[s * np + i] = B[i * nsamp + s];
     for (int k = 0; k < 3; k++)
         for (int i = 0; i < np; i++) O->Vint[k * np + i] = B[i * nsamp + 3 * pt + k];
-    free(B); free(Vd); free(VdT); free(pv);
+    free(B); free(Vd);
+    O->VdLU = VdT;  /* kept for the node interpolant at arbitrary (u, v) */
+    O->VdPiv = pv;
     return 0;
 }
 
 static void order_free(orc_order *O) {
     free(O->Eint);
     free(O->Vint);
-    O->Eint = O->Vint = NULL;
+    free(O->VdLU);
+    free(O->VdPiv);
+    O->Eint = O->Vint = O->VdLU = NULL;
+    O->VdPiv = NULL;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -834,6 +841,63 @@ static void omega0_edge(const orc_order *O, const double *ea, int p, const doubl
 /* Steps 4-8 for one (target, patch) pair                                     */
 /* ------------------------------------------------------------------------- */
 
+/* Node interpolant of patch P at (u, v) in the local frame: X = sum_i l_i(u,v) y_i,
+ * the Lagrange functions l_i from the Dubiner basis and the nodes' Vandermonde. */
+static void node_interp(const orc_order *O, const orc_patch *P, double u, double v, double X[3]) {
+    double psi[ORC_PMAX * ORC_PMAX];
+    dubiner(P->p - 1, u, v, psi);
+    lu_solve(P->np, O->VdLU, O->VdPiv, 1, psi);
+    X[0] = X[1] = X[2] = 0.0;
+    for (int i = 0; i < P->np; i++)
+        for (int a = 0; a < 3; a++) X[a] += psi[i] * P->y[3 * i + a];
+}
+
+/* Side of the patch on which the target lies, seen along the frame axis e_z.  The
+ * point of the patch with the target's in-plane coordinates (its footprint) is found
+ * by Newton on the in-plane part of the node interpolant, from the target's
+ * barycentric coordinates in the projected vertex triangle (finite-difference
+ * Jacobian).  Returns +1 if the footprint lies in the patch and the target is on or
+ * above it, -1 if below it, 0 if the footprint is outside the patch or Newton fails. */
+static int footprint_side(const orc_order *O, const orc_patch *P, const double yt[3]) {
+    double vx[3][3];
+    for (int k = 0; k < 3; k++)
+        for (int a = 0; a < 3; a++) {
+            vx[k][a] = 0.0;
+            for (int i = 0; i < P->np; i++) vx[k][a] += O->Vint[k * P->np + i] * P->y[3 * i + a];
+        }
+    double a11 = vx[1][0] - vx[0][0], a12 = vx[2][0] - vx[0][0];
+    double a21 = vx[1][1] - vx[0][1], a22 = vx[2][1] - vx[0][1];
+    double det = a11 * a22 - a12 * a21;
+    if (det == 0.0) return 0;
+    double rx = yt[0] - vx[0][0], ry = yt[1] - vx[0][1];
+    double u = (a22 * rx - a12 * ry) / det, v = (a11 * ry - a21 * rx) / det;
+    int conv = 0;
+    for (int it = 0; it < 30; it++) {
+        const double h = 1e-6;
+        double X[3], Xup[3], Xum[3], Xvp[3], Xvm[3];
+        node_interp(O, P, u, v, X);
+        node_interp(O, P, u + h, v, Xup);
+        node_interp(O, P, u - h, v, Xum);
+        node_interp(O, P, u, v + h, Xvp);
+        node_interp(O, P, u, v - h, Xvm);
+        double j11 = (Xup[0] - Xum[0]) / (2 * h), j12 = (Xvp[0] - Xvm[0]) / (2 * h);
+        double j21 = (Xup[1] - Xum[1]) / (2 * h), j22 = (Xvp[1] - Xvm[1]) / (2 * h);
+        double dj = j11 * j22 - j12 * j21;
+        if (dj == 0.0) break;
+        double fx = X[0] - yt[0], fy = X[1] - yt[1];
+        double du = (j22 * fx - j12 * fy) / dj, dv = (j11 * fy - j21 * fx) / dj;
+        u -= du;
+        v -= dv;
+        if (fabs(du) + fabs(dv) <= 1e-14 * (1.0 + fabs(u) + fabs(v))) { conv = 1; break; }
+    }
+    if (!conv) return 0;
+    const double tol = 1e-12;
+    if (u < -tol || v < -tol || u + v > 1.0 + tol) return 0;
+    double X[3];
+    node_interp(O, P, u, v, X);
+    return yt[2] >= X[2] ? 1 : -1;
+}
+
 /* Quantities of Steps 4-7 for one pair: per lm (1<=m<=l<=p, lm = l(l-1)/2+m-1)
  * B[lm][4] = int over dP of beta^{(l,m)} (Thm. dlp1form, eq. dlp1formrep2),
  * Psi[lm]  = int over dP of psi^{(l,m)} (Thm. cslp1form),
@@ -869,9 +933,15 @@ static int pair_forms(const orc_order *O, const orc_patch *P, const orc_opts *op
             grad_S(St, p, l, m, gSt[HIDX(l, m)]);
             if (want_dp) hess_S(St, p, l, m, HSt[HIDX(l, m)]);
         }
-    /* choice of u (Thm. dlp1form) */
+    /* choice of u (Thm. dlp1form): the half-line from the target along u must not meet
+       the patch.  +e_z for a node of the patch (exterior limit); if the target's
+       footprint along e_z lies in the patch, the side the target is on; otherwise the
+       better of +-e_z by the smallest u.(r'-r)/|r'-r| over nodes and edge samples. */
     double u[3] = {0, 0, 1};
-    {
+    const int side = self_i < 0 ? footprint_side(O, P, yt) : 0;
+    if (side != 0) {
+        u[2] = side;
+    } else {
         double mplus = 2, mminus = 2;
         for (int s = 0; s < np + 3 * pt; s++) {
             const double *r = s < np ? P->y + 3 * s : P->ey + 3 * (s - np);
