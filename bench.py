@@ -125,29 +125,33 @@ class ClockSampler:
 
 
 def flops_per_pair(p: int) -> float:
-    """Algorithmic FP64 flop count of one (target, patch) pair for all four kernels,
-    counted from the loop structure of the per-pair kernel (Steps 4-8); the graded
-    Omega_0 panels are counted separately per panel point."""
+    """Algorithmic FP64 flops of one (target, patch) pair for all four kernels, counted
+    from the loops of the per-pair stage (an FMA is 2 flops; work that the kernel repeats
+    but need not is counted once).  Not counted: the graded Omega_0 panels and the
+    upsampled rule of far edges (their cost depends on the geometry), index arithmetic."""
     np_ = p * (p + 1) // 2
     pt = 2 * p
     njk = (p + 1) * (p + 2) // 2
     ns = 3 * pt
-    n2 = sum(j + 1 for j in range(2, p + 1))          # (j,k>=0) with j >= 2
-    n1 = sum(j + 1 for j in range(1, p + 1))          # (j,k>=0) with j >= 1
-    line = ns * (n1 * 16 + n2 * (60 + 64))            # V; Q and dQ per sample and harmonic
+    n1, n2 = njk - 1, njk - 3                          # harmonics (j, k >= 0) with j >= 1, j >= 2
+    # Step 6: V (3 FMA x complex) for j >= 1; Q (18 FMA) and dQ/dnu' (24 FMA) for j >= 2
+    line = ns * (12 * n1 + 36 * n2 + 48 * n2)
+    # Step 7: per (l, m >= 1), sum over (j, k): 5 flops for the psi term, 67 with Q, dQ, dS (j >= 2)
     trans = 0
     for l in range(1, p + 1):
         for m in range(1, l + 1):
             for j in range(1, l + 1):
                 kmin, kmax = max(-j, m - (l - j)), min(j, m + (l - j))
-                nk = max(0, kmax - kmin + 1)
-                trans += nk * (8 + (2 * 4 * 8 if j >= 2 else 0) + (4 * 16 if j >= 2 else 0))
-    contract = np_ * np_ * (8 + 8 + 16 + 12)          # D, D', S', S rows through the fit matrices
-    weights = 3 * (pt * pt * 4 + pt * 12)             # lambda = U^T I (m = 1, 3) and ratios
-    harm = njk * 60 + (np_ + ns) * 8                  # target table, gradients/Hessians, u choice
-    root = 3 * 8 * (3 * p * 16 + 20)                  # ~8 Newton steps of the complex edge polynomial
-    smooth = np_ * 40
-    return float(line + trans + contract + weights + harm + root + smooth)
+                trans += max(0, kmax - kmin + 1) * (67 if j >= 2 else 5)
+    trans += np_ * 100                                 # I[gamma] and its nu' derivative per (l, m)
+    # Step 8: per (node, (l, m)) 4-term dot products for D, D', S', S; jump and smooth rule per node
+    rows = np_ * np_ * 34 + np_ * 60
+    weights = 3 * (pt * pt * 4 + pt * 30)              # lambda = U^T I for m = 1, 3 and the ratios
+    moments = 3 * 20 * pt                              # J_i, K_i recurrences
+    harm = ns * 12 + njk * (8 + 36)                    # samples, target table, gradients, Hessians
+    u_choice = (np_ + ns) * 10
+    root = 3 * 4 * (48 * p + 20)                       # ~4 Newton steps on the complex edge polynomial
+    return float(line + trans + rows + weights + moments + harm + u_choice + root)
 
 
 def bench_gpu(args):
@@ -194,6 +198,7 @@ def bench_gpu(args):
         times.append(e0.elapsed_time(e1))
         pair_ms.append(ctx.diagnostics()["ms_pairs"])
     torch.cuda.synchronize(dev)
+    diag = ctx.diagnostics()           # stage times and launch count of the last FP64 build
     if world > 1:
         torch.distributed.barrier()
     # the mixed-precision build (line integrals in double-float FP32) on the same inputs
@@ -211,7 +216,7 @@ def bench_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    diag = ctx.diagnostics()
+    mdiag = ctx.diagnostics()
     ms_step = reduce_max(sum(times) / len(times), world, dev)
     entries = nnz * len(KERNELS)
     total_entries = reduce_sum(float(entries), world, dev)
@@ -232,6 +237,8 @@ def bench_gpu(args):
     achieved = fpp * npairs / pair_s / 1e12
     # kernel launches per step: per-order precompute and pair kernels, near list, scans, items
     launches = diag.get("kernel_launches", None)
+    apply = None if args.no_apply else apply_leg(ctx, surf, targ, d, tg, dev)
+    batched = None if (args.no_batched or world > 1) else batched_leg(ctx, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -241,14 +248,18 @@ def bench_gpu(args):
                    "l2": "512 MB flush between timed steps", "parallelism": f"weak x{world}"},
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_pairs<6>",
+                     "traffic": None, "kernel": "k_roots<6> + k_pairs_tile<6, false> (one per-pair stage)",
                      "peak_note": "measured FP64 FMA peak (rrq_measure_fma_peak); FP32 FMA peak %.1f TFLOP/s" % peak32,
                      "flops_per_pair": fpp, "kernel_ms": pair_s * 1e3},
         "stage_ms": {"precompute": diag["ms_precompute"], "near_and_items": diag["ms_near"], "pairs": diag["ms_pairs"]},
         "clocks": clk,
         "gpu_launches": launches * args.steps if launches is not None else None,
         "points_per_s": world * tg.n / (ms_step * 1e-3),
+        "apply": apply,
+        "batched": batched,
         "mixed": {"value": total_entries / (ms_mixed * 1e-3), "unit": UNIT, "ms_per_step": ms_mixed,
+                  "stage_ms": {"precompute": mdiag["ms_precompute"], "near_and_items": mdiag["ms_near"],
+                               "pairs": mdiag["ms_pairs"]},
                   "speedup_vs_fp64": ms_step / ms_mixed,
                   "precision": "Step-6 line integrals in double-float FP32 (about 48 bits), rest FP64",
                   "parity": "apply-level error as FP64; rows within 32x the oracle's own rounding sensitivity "
@@ -262,6 +273,91 @@ def bench_gpu(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def apply_leg(ctx, surf, targ, d, tg, dev, reps: int = 3) -> dict:
+    """The apply (y = smooth direct sum + CSR correction times sigma) for each kernel on
+    the FP64 corrections of this workload, timed per device kernel by the library's own
+    CUDA events: SpMV against the measured HBM copy bandwidth, the direct sum in
+    interactions/s.  The CSR (about 1.1 GB per kernel) is larger than L2."""
+    import torch
+    csr = ctx.build_corrections(surf, targ, KERNELS)
+    nnz = csr.nnz
+    sig = torch.as_tensor(np.random.default_rng(SEED + 7).standard_normal(d.nnode), dtype=torch.float64,
+                          device=dev)
+    out = torch.empty(tg.n, dtype=torch.float64, device=dev)
+    spmv, smooth = [], []
+    for k in KERNELS:
+        for it in range(reps + 1):
+            ctx.apply(surf, targ, k, csr, sig, out)
+            dg = ctx.diagnostics()
+            if it > 0:
+                spmv.append(dg["ms_apply_spmv"])
+                smooth.append(dg["ms_apply_smooth"])
+    ctx.csr_free(csr)
+    ms_spmv = statistics.median(spmv)
+    ms_smooth = statistics.median(smooth)
+    # algorithmic bytes of one SpMV: val (8) + col (4) per entry, rowptr, out read + write, sigma
+    spmv_bytes = nnz * 12 + (tg.n + 1) * 8 + tg.n * 16 + d.nnode * 8
+    peak = measured_peaks().get("hbm_gbs")
+    gbs = spmv_bytes / (ms_spmv * 1e-3) / 1e9
+    return {"spmv": {"ms": ms_spmv, "nnz": nnz, "bytes": spmv_bytes, "achieved_gbs": gbs, "peak_gbs": peak,
+                     "frac": gbs / peak if peak else None, "peak_note": "of measured HBM copy bandwidth"},
+            "direct_sum": {"ms": ms_smooth, "interactions_per_s": tg.n * d.nnode / (ms_smooth * 1e-3),
+                           "note": "dense smooth rule over all N_T x N_S pairs (the paper uses an FMM here)"}}
+
+
+def batched_leg(ctx, dev) -> dict:
+    """The batched form: 64 seeded star surfaces (80..5120 patches, p in {4, 6, 8}, all
+    on-surface nodes as targets) in one plan (rrq_batch_create: near lists, CSR structure,
+    autotuned launch shapes, value computation recorded as one CUDA graph), executed
+    after one warm-up execution, FP64 and mixed; against building the same surfaces one
+    by one with rrq_build_corrections in FP64.  Device times by CUDA events."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    from paper_2411_08342_gb300 import workloads as W
+    items = W.star_batch()
+    arrs = [rrq.device_inputs(d, tg, device=str(dev)) for d, tg in items]
+    surfs = [ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv)
+             for a, (d, _) in zip(arrs, items)]
+    targs = [ctx.targets(a["txyz"], a["tnrm"], a["tself"]) for a in arrs]
+    out = {"workload": "star_batch64 (80..5120 patches, p in {4,6,8}, on-surface nodes)",
+           "surfaces": len(items), "targets": int(sum(tg.n for _, tg in items))}
+    entries = 0
+    for mixed in (False, True):
+        b = ctx.batch(surfs, targs, mixed=mixed, autotune=True)
+        b.execute()
+        b.execute()
+        ms = ctx.diagnostics()["ms_pairs"]
+        info = b.info()
+        entries = info["nnz"] * len(KERNELS)
+        out["mixed" if mixed else "fp64"] = {
+            "value": entries / (ms * 1e-3), "unit": UNIT, "ms_execute": ms, "ms_create": info["ms_create"],
+            "ms_autotune": info["ms_autotune"], "graph_kernels": info["graph_kernels"],
+            "tile": {p: info["tile"][p] for p in (4, 6, 8)},
+            "persistent": {p: info["persistent"][p] for p in (4, 6, 8)}}
+        out["pairs"] = info["npairs"]
+        out["nnz_per_kernel"] = info["nnz"]
+        b.close()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(torch.cuda.current_stream(dev))
+    for sf, tg in zip(surfs, targs):
+        ctx.csr_free(ctx.build_corrections(sf, tg, KERNELS))
+    ev1.record(torch.cuda.current_stream(dev))
+    ev1.synchronize()
+    ms_loop = ev0.elapsed_time(ev1)
+    out["one_by_one_fp64"] = {"value": entries / (ms_loop * 1e-3), "unit": UNIT, "ms": ms_loop}
+    out["speedup_batched_mixed_vs_one_by_one_fp64"] = out["mixed"]["value"] / out["one_by_one_fp64"]["value"]
+    return out
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def e2e_leg(ctx, d, tg, nnz, dev, flush, args, world, total_entries):
@@ -352,6 +448,8 @@ def main():
     ap.add_argument("--cpu-targets", type=int, default=40000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-apply", action="store_true", help="skip the apply (SpMV + direct sum) timing")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-surface batched build")
     ap.add_argument("--ntarg", type=int, default=NTARG, help="targets per rank (default: the workload's 200k)")
     args = ap.parse_args()
     if args.impl == "reference":

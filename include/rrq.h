@@ -122,6 +122,7 @@ typedef struct {
     int64_t far_edges;       /* edges evaluated by the upsampled Gauss rule */
     double ms_near, ms_precompute, ms_pairs;  /* stage times of the last build (ms) */
     int64_t kernel_launches; /* CUDA kernels the last build launched */
+    double ms_apply_smooth, ms_apply_spmv;    /* kernel times of the last rrq_apply (ms) */
 } rrq_diag;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
@@ -139,14 +140,16 @@ void rrq_ctx_destroy(rrq_ctx *ctx);
 rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
                                  uint32_t kernel_mask, const rrq_options *opt, rrq_csr *out);
 
-/* Copy a CSR (built by rrq_build_corrections) into caller buffers: rowptr [nrows+1],
- * col [nnz], val[k] [nnz] for each built kernel k (NULL entries are skipped).
+/* Copy a CSR (built by rrq_build_corrections, or a batch view) into caller buffers:
+ * rowptr [nrows+1] (rebased to start at 0), col [nnz], val[k] [nnz] for each built
+ * kernel k (NULL entries are skipped).
  * dst_on_host = 1 for host buffers (pinned or pageable), 0 for device buffers.
  * Synchronises the context stream. */
 rrq_status rrq_csr_copy(rrq_ctx *ctx, const rrq_csr *csr, int64_t *rowptr, int32_t *col,
                         double *val[4], int32_t dst_on_host);
 
-/* Free the device buffers of a CSR built by this context and zero the struct. */
+/* Free the device buffers of a CSR built by this context and zero the struct
+ * (RRQ_ERR_ARG for a batch view). */
 rrq_status rrq_csr_free(rrq_ctx *ctx, rrq_csr *csr);
 
 /* Apply one corrected operator (Sec. 5, eq. dlpsplitting):
@@ -189,6 +192,61 @@ rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surface *surf, c
                                         uint32_t kernel_mask, const rrq_options *opt, int64_t *rowptr,
                                         int32_t *col, double *val[4], int64_t capacity, int64_t *nnz_out,
                                         int64_t *npairs_out);
+
+/* ---- Batched build of many surfaces (the paper has no counterpart: it builds one
+ * surface at a time).  A batch plan takes nsurf surfaces, each with its own targets,
+ * patch counts and orders, and runs the same per-patch and per-pair computation as
+ * rrq_build_corrections over all of them at once:
+ *   - rrq_batch_create checks and copies the inputs into batch-owned device memory,
+ *     computes the patch bounds, builds every surface's near list (a target sees only
+ *     the patches of its own surface), the CSR structure of the whole batch and the
+ *     pair work list (grouped by order, then patch), then records the value
+ *     computation -- per-patch precompute of every order, then for every order one
+ *     root kernel and one persistent pair kernel over the pairs of all surfaces (S, D,
+ *     S', D' in one pass per pair) -- as one CUDA graph.  With RRQ_BATCH_AUTOTUNE in
+ *     `flags` it first times the compiled tile sizes (pairs per CTA) and both schedules
+ *     (persistent / 16 waves) of every order on a sample of that order's pairs and
+ *     records the fastest; otherwise each order takes its default shape, persistent;
+ *   - rrq_batch_execute launches that graph once and synchronises: afterwards the
+ *     batch CSR holds the corrections of every surface.  Executing again recomputes
+ *     the same values (the graph reads only batch-owned copies of the inputs);
+ *   - the result is ONE CSR over the concatenated targets: rows row_start[s] ..
+ *     row_start[s+1]-1 belong to surface s, and their columns are node ids LOCAL to
+ *     surface s, so rrq_batch_csr(b, s, &view) gives a CSR view of surface s that
+ *     rrq_apply accepts together with that surface and its targets.  Views alias the
+ *     batch's memory: never pass them to rrq_csr_free; they live until
+ *     rrq_batch_destroy.
+ * All surfaces must use the same reference nodes for a given order (RRQ_ERR_ARG
+ * otherwise).  Each targets' self_node holds node ids of its own surface.  Options and
+ * errors as rrq_build_corrections; rrq_batch_create synchronises the context stream.
+ * rrq_last_diagnostics after rrq_batch_execute reports that execution (counters;
+ * ms_pairs = device time of the whole graph, precompute included; kernel_launches =
+ * kernel nodes in the graph). */
+typedef struct rrq_batch rrq_batch;
+enum { RRQ_BATCH_AUTOTUNE = 1 };
+/* Set in rrq_csr.kernel_mask of a view: its rowptr values index the batch's col/val
+ * arrays (rowptr[0] may be nonzero) and rrq_csr_free refuses it. */
+#define RRQ_CSR_VIEW 0x80000000u
+
+typedef struct {
+    int32_t nsurf;
+    int64_t nrows, nnode, nnz, npairs;   /* totals over the batch */
+    int32_t graph_kernels;               /* kernel nodes in the recorded graph */
+    int32_t tile[RRQ_PMAX + 1];          /* pairs per CTA chosen for order p (0: order absent) */
+    int32_t persistent[RRQ_PMAX + 1];    /* 1: one wave of CTAs fetching tiles from a counter */
+    double ms_create, ms_autotune;       /* host wall time of rrq_batch_create and of its tuning */
+    double ms_last_execute;              /* device time of the last rrq_batch_execute */
+} rrq_batch_info;
+
+rrq_status rrq_batch_create(rrq_ctx *ctx, int32_t nsurf, const rrq_surface *surfs, const rrq_targets *targs,
+                            uint32_t kernel_mask, const rrq_options *opt, uint32_t flags, rrq_batch **out);
+rrq_status rrq_batch_execute(rrq_ctx *ctx, rrq_batch *batch);
+/* surf in [0, nsurf): view of that surface's rows; surf = -1: the whole batch.
+ * row_start, node_start (may be NULL): [nsurf+1] host arrays of first rows / nodes. */
+rrq_status rrq_batch_csr(const rrq_batch *batch, int32_t surf, rrq_csr *view, int64_t *row_start,
+                         int64_t *node_start);
+rrq_status rrq_batch_info_get(const rrq_batch *batch, rrq_batch_info *info);
+void rrq_batch_destroy(rrq_batch *batch);
 
 /* Measured fused-multiply-add throughput of this device in TFLOP/s (2 flops per FMA),
  * FP64 (fp32 = 0) or FP32 (fp32 = 1): 8 independent dependency chains per thread,

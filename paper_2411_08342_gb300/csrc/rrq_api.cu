@@ -8,27 +8,19 @@
 #include <algorithm>
 #include <vector>
 
-#include "rrq_internal.cuh"
+#include "rrq_host.h"
 
-// near-list and scan helpers (rrq_near.cu)
-struct NearBuffers {
-    int64_t *poff;
-    int32_t *pairs;
-    int64_t npairs;
-};
-typedef void *(*rrq_alloc_fn)(void *ctx, size_t bytes);
-cudaError_t rrq_near_build(const double *d_bounds, int npatch, const int64_t *d_node_off, const double *d_txyz,
-                           const int64_t *d_tself, int64_t ntarg, double eta, rrq_alloc_fn alloc, void *actx,
-                           NearBuffers *out, cudaStream_t st);
-cudaError_t rrq_items_build(const NearBuffers *nb, int64_t ntarg, const int32_t *d_order, const int32_t *d_rank,
-                            int npatch, rrq_alloc_fn alloc, void *actx, int64_t *d_rowptr, PairItem **items_out,
-                            int64_t **rank_off_out, cudaStream_t st);
 
-#define RRQ_DECL_PAIRS(P)                                                                                        \
-    cudaError_t rrq_launch_pairs_p##P(const OrderTables *, const PairItem *, int64_t, PatchData, const int64_t *, \
-                                      const double *, const double *, const double *, const double *,           \
-                                      const double *, const int64_t *, uint32_t, int, double *, double *,       \
-                                      double *, double *, int32_t *, BuildCounters *, cudaStream_t);
+
+
+
+static thread_local char g_err[RRQ_ERR_LEN] = "";
+char *rrq_err_buf() { return g_err; }
+void set_err(const char *what, cudaError_t e) { snprintf(g_err, RRQ_ERR_LEN, "%s: %s", what, cudaGetErrorString(e)); }
+
+#define RRQ_DECL_PAIRS(P)                                                                              \
+    cudaError_t rrq_launch_pairs_p##P(bool, const PairArgs &, const PairShape &, cudaStream_t); \
+    int rrq_pair_tiles_p##P(int out[4]);
 RRQ_DECL_PAIRS(2)
 RRQ_DECL_PAIRS(3)
 RRQ_DECL_PAIRS(4)
@@ -36,182 +28,26 @@ RRQ_DECL_PAIRS(5)
 RRQ_DECL_PAIRS(6)
 RRQ_DECL_PAIRS(7)
 RRQ_DECL_PAIRS(8)
-#define RRQ_DECL_PAIRS_MIX(P)                                                                                    \
-    cudaError_t rrq_launch_pairs_mix_p##P(const OrderTables *, const PairItem *, int64_t, PatchData,            \
-                                          const int64_t *, const double *, const double *, const double *,      \
-                                          const double *, const double *, const int64_t *, uint32_t, int,       \
-                                          double *, double *, double *, double *, int32_t *, BuildCounters *,   \
-                                          cudaStream_t);
-RRQ_DECL_PAIRS_MIX(2)
-RRQ_DECL_PAIRS_MIX(3)
-RRQ_DECL_PAIRS_MIX(4)
-RRQ_DECL_PAIRS_MIX(5)
-RRQ_DECL_PAIRS_MIX(6)
-RRQ_DECL_PAIRS_MIX(7)
-RRQ_DECL_PAIRS_MIX(8)
+#undef RRQ_DECL_PAIRS
 
-cudaError_t rrq_launch_pairs_mix(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
-                                 const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
-                                 const double *d_wts, const double *d_txyz, const double *d_tnrm,
-                                 const int64_t *d_tself, uint32_t mask, int newton_max, double *vS, double *vD,
-                                 double *vSp, double *vDp, int32_t *col, BuildCounters *cnt, cudaStream_t st) {
-#define RRQ_CASEM(P)                                                                                                 \
-    case P:                                                                                                          \
-        return rrq_launch_pairs_mix_p##P(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts, d_txyz,        \
-                                         d_tnrm, d_tself, mask, newton_max, vS, vD, vSp, vDp, col, cnt, st);
+cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape shape, cudaStream_t st) {
     switch (p) {
-        RRQ_CASEM(2) RRQ_CASEM(3) RRQ_CASEM(4) RRQ_CASEM(5) RRQ_CASEM(6) RRQ_CASEM(7) RRQ_CASEM(8)
-        default: return cudaErrorInvalidValue;
-    }
-#undef RRQ_CASEM
-}
-
-cudaError_t rrq_launch_pairs(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
-                             const int64_t *d_node_off, const double *d_xyz, const double *d_nrm, const double *d_wts,
-                             const double *d_txyz, const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
-                             int newton_max, double *vS, double *vD, double *vSp, double *vDp, int32_t *col,
-                             BuildCounters *cnt, cudaStream_t st) {
-#define RRQ_CASE(P)                                                                                                  \
-    case P:                                                                                                          \
-        return rrq_launch_pairs_p##P(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts, d_txyz, d_tnrm,    \
-                                     d_tself, mask, newton_max, vS, vD, vSp, vDp, col, cnt, st);
-    switch (p) {
+#define RRQ_CASE(P) \
+    case P: return rrq_launch_pairs_p##P(mixed, a, shape, st);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
+#undef RRQ_CASE
         default: return cudaErrorInvalidValue;
     }
+}
+
+int rrq_pair_tiles(int p, int tiles[4]) {
+    switch (p) {
+#define RRQ_CASE(P) \
+    case P: return rrq_pair_tiles_p##P(tiles);
+        RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
 #undef RRQ_CASE
-}
-
-static thread_local char g_err[512] = "";
-
-static void set_err(const char *what, cudaError_t e) {
-    snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
-}
-
-struct rrq_ctx {
-    int device;
-    cudaStream_t stream;
-    rrq_diag diag;
-    cudaEvent_t ev[4];
-    // cached per-order tables
-    OrderTables *d_tab[RRQ_PMAX + 1];
-    std::vector<double> tab_key[RRQ_PMAX + 1];
-    double tab_rho0[RRQ_PMAX + 1];
-};
-
-// scratch allocator: stream-ordered allocations freed together
-struct Scratch {
-    cudaStream_t st;
-    std::vector<void *> ptrs;
-    bool failed = false;
-    static void *alloc(void *self, size_t bytes) {
-        Scratch *s = static_cast<Scratch *>(self);
-        void *p = nullptr;
-        if (bytes == 0) bytes = 16;
-        if (cudaMallocAsync(&p, bytes, s->st) != cudaSuccess) {
-            s->failed = true;
-            cudaGetLastError();
-            return nullptr;
-        }
-        s->ptrs.push_back(p);
-        return p;
+        default: return 0;
     }
-    ~Scratch() {
-        for (void *p : ptrs) cudaFreeAsync(p, st);
-    }
-};
-
-#define CK(call)                                   \
-    do {                                           \
-        cudaError_t _e = (call);                   \
-        if (_e != cudaSuccess) {                   \
-            set_err(#call, _e);                    \
-            return _e == cudaErrorMemoryAllocation ? RRQ_ERR_OOM : RRQ_ERR_CUDA; \
-        }                                          \
-    } while (0)
-
-extern "C" {
-
-const char *rrq_status_string(rrq_status s) {
-    switch (s) {
-        case RRQ_OK: return "ok";
-        case RRQ_ERR_ARG: return "invalid argument";
-        case RRQ_ERR_CUDA: return "CUDA error";
-        case RRQ_ERR_OOM: return "out of device memory";
-        case RRQ_ERR_DEGENERATE: return "degenerate patch or singular fit";
-        case RRQ_ERR_UNSUPPORTED: return "unsupported option";
-        case RRQ_WARN_ROOTFIND: return "ok, some edges used the fallback rule";
-        default: return "unknown status";
-    }
-}
-
-const char *rrq_last_error(void) { return g_err; }
-
-rrq_status rrq_ctx_create(rrq_ctx **ctx, int device, void *cuda_stream) {
-    if (!ctx) return RRQ_ERR_ARG;
-    *ctx = nullptr;
-    int ndev = 0;
-    CK(cudaGetDeviceCount(&ndev));
-    if (device < 0 || device >= ndev) return RRQ_ERR_ARG;
-    CK(cudaSetDevice(device));
-    rrq_ctx *c = new rrq_ctx();
-    c->device = device;
-    c->stream = (cudaStream_t)cuda_stream;
-    memset(&c->diag, 0, sizeof(c->diag));
-    for (int p = 0; p <= RRQ_PMAX; p++) { c->d_tab[p] = nullptr; c->tab_rho0[p] = -1; }
-    for (int i = 0; i < 4; i++) cudaEventCreate(&c->ev[i]);
-    // keep freed stream-ordered memory in the pool between builds
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-        uint64_t thr = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    *ctx = c;
-    return RRQ_OK;
-}
-
-void rrq_ctx_destroy(rrq_ctx *ctx) {
-    if (!ctx) return;
-    cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
-    for (int p = 0; p <= RRQ_PMAX; p++)
-        if (ctx->d_tab[p]) cudaFree(ctx->d_tab[p]);
-    for (int i = 0; i < 4; i++) cudaEventDestroy(ctx->ev[i]);
-    delete ctx;
-}
-
-rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag) {
-    if (!ctx || !diag) return RRQ_ERR_ARG;
-    *diag = ctx->diag;
-    return RRQ_OK;
-}
-
-}  // extern "C"
-
-namespace {
-
-int np_of(int p) { return p * (p + 1) / 2; }
-
-// device views of the inputs (copies when they were host pointers)
-struct Inputs {
-    int npatch;
-    int64_t nnode, ntarg;
-    std::vector<int32_t> h_order;
-    std::vector<int64_t> h_node_off;
-    const int32_t *order;
-    const int64_t *node_off;
-    const double *xyz, *nrm, *wts, *txyz, *tnrm;
-    const int64_t *tself;
-};
-
-template <typename T>
-const T *upload(Scratch &s, const T *h, size_t n, bool on_host, cudaError_t *err) {
-    if (!on_host || n == 0) return h;
-    T *d = (T *)Scratch::alloc(&s, sizeof(T) * n);
-    if (!d) { *err = cudaErrorMemoryAllocation; return nullptr; }
-    cudaError_t e = cudaMemcpyAsync(d, h, sizeof(T) * n, cudaMemcpyHostToDevice, s.st);
-    if (e != cudaSuccess) *err = e;
-    return d;
 }
 
 rrq_status prepare_inputs(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const rrq_targets *targ, bool on_host,
@@ -276,7 +112,65 @@ rrq_status order_tables(rrq_ctx *ctx, int p, const double *ref_uv, double rho0) 
     return RRQ_OK;
 }
 
-}  // namespace
+
+extern "C" {
+
+const char *rrq_status_string(rrq_status s) {
+    switch (s) {
+        case RRQ_OK: return "ok";
+        case RRQ_ERR_ARG: return "invalid argument";
+        case RRQ_ERR_CUDA: return "CUDA error";
+        case RRQ_ERR_OOM: return "out of device memory";
+        case RRQ_ERR_DEGENERATE: return "degenerate patch or singular fit";
+        case RRQ_ERR_UNSUPPORTED: return "unsupported option";
+        case RRQ_WARN_ROOTFIND: return "ok, some edges used the fallback rule";
+        default: return "unknown status";
+    }
+}
+
+const char *rrq_last_error(void) { return rrq_err_buf(); }
+
+rrq_status rrq_ctx_create(rrq_ctx **ctx, int device, void *cuda_stream) {
+    if (!ctx) return RRQ_ERR_ARG;
+    *ctx = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return RRQ_ERR_ARG;
+    CK(cudaSetDevice(device));
+    rrq_ctx *c = new rrq_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    memset(&c->diag, 0, sizeof(c->diag));
+    for (int p = 0; p <= RRQ_PMAX; p++) { c->d_tab[p] = nullptr; c->tab_rho0[p] = -1; }
+    for (int i = 0; i < 4; i++) cudaEventCreate(&c->ev[i]);
+    // keep freed stream-ordered memory in the pool between builds
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *ctx = c;
+    return RRQ_OK;
+}
+
+void rrq_ctx_destroy(rrq_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (int p = 0; p <= RRQ_PMAX; p++)
+        if (ctx->d_tab[p]) cudaFree(ctx->d_tab[p]);
+    for (int i = 0; i < 4; i++) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+}
+
+rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag) {
+    if (!ctx || !diag) return RRQ_ERR_ARG;
+    *diag = ctx->diag;
+    return RRQ_OK;
+}
+
+}  // extern "C"
+
 
 extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
                                             uint32_t kernel_mask, const rrq_options *opt, rrq_csr *out) {
@@ -318,12 +212,13 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
         }
     // patch data
     const size_t NPc = in.npatch;
-    PatchData pd;
+    PatchData pd{};
     pd.npatch = in.npatch;
     pd.pmax = pmax;
     pd.frame = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_FRAME);
     pd.bounds = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_BOUNDS);
     pd.ynode = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
+    pd.xm = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
     pd.ea = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ea());
     pd.ey = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
     pd.et = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
@@ -405,7 +300,8 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
         return RRQ_ERR_OOM;
     }
     EdgeRoot *roots = (EdgeRoot *)Scratch::alloc(&s, sizeof(EdgeRoot) * 3 * (nb.npairs > 0 ? nb.npairs : 1));
-    if (!roots) oom = true;
+    int8_t *uside = (int8_t *)Scratch::alloc(&s, sizeof(int8_t) * (nb.npairs > 0 ? nb.npairs : 1));
+    if (!roots || !uside) oom = true;
     if (oom) {
         cudaFreeAsync(d_rowptr, s.st);
         cudaFreeAsync(col, s.st);
@@ -421,9 +317,11 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
                 int64_t i0 = h_roff[start], i1 = h_roff[start + n];
                 PatchData pdo = pd;
                 pdo.roots = roots + 3 * i0;
-                e = (mixed ? rrq_launch_pairs_mix : rrq_launch_pairs)(
-                    p, ctx->d_tab[p], items + i0, i1 - i0, pdo, in.node_off, in.xyz, in.nrm, in.wts, in.txyz, in.tnrm,
-                    in.tself, kernel_mask, newton_max, vals[0], vals[1], vals[2], vals[3], col, d_cnt, s.st);
+                pdo.uside = uside + i0;
+                const PairArgs pa = {ctx->d_tab[p], items + i0, i1 - i0, pdo, in.node_off, in.xyz, in.nrm, in.wts,
+                                     in.txyz, in.tnrm, in.tself, kernel_mask, newton_max,
+                                     {vals[0], vals[1], vals[2], vals[3]}, col, d_cnt};
+                e = rrq_launch_pairs(p, mixed, pa, PairShape{0, 0, nullptr}, s.st);
                 if (e != cudaSuccess) break;
             }
             start += n;
@@ -466,22 +364,42 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
 }
 
+namespace {
+__global__ void k_rebase(int64_t *rowptr, int64_t n, int64_t first) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rowptr[i] -= first;
+}
+}  // namespace
+
 extern "C" rrq_status rrq_csr_copy(rrq_ctx *ctx, const rrq_csr *csr, int64_t *rowptr, int32_t *col, double *val[4],
                                    int32_t dst_on_host) {
     if (!ctx || !csr) return RRQ_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     cudaMemcpyKind kind = dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    // a batch view indexes the batch's col/val arrays: its entries start at rowptr[0]
+    int64_t first = 0;
+    if ((csr->kernel_mask & RRQ_CSR_VIEW) && csr->rowptr) {
+        CK(cudaMemcpyAsync(&first, csr->rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     if (rowptr && csr->rowptr) CK(cudaMemcpyAsync(rowptr, csr->rowptr, sizeof(int64_t) * (csr->nrows + 1), kind, ctx->stream));
-    if (col && csr->col && csr->nnz) CK(cudaMemcpyAsync(col, csr->col, sizeof(int32_t) * csr->nnz, kind, ctx->stream));
+    if (col && csr->col && csr->nnz)
+        CK(cudaMemcpyAsync(col, csr->col + first, sizeof(int32_t) * csr->nnz, kind, ctx->stream));
     for (int k = 0; k < 4; k++)
         if (val && val[k] && csr->val[k] && csr->nnz)
-            CK(cudaMemcpyAsync(val[k], csr->val[k], sizeof(double) * csr->nnz, kind, ctx->stream));
+            CK(cudaMemcpyAsync(val[k], csr->val[k] + first, sizeof(double) * csr->nnz, kind, ctx->stream));
+    if (rowptr && csr->rowptr && first != 0 && !dst_on_host) {
+        k_rebase<<<(unsigned)((csr->nrows + 256) / 256), 256, 0, ctx->stream>>>(rowptr, csr->nrows + 1, first);
+        CK(cudaGetLastError());
+    }
     CK(cudaStreamSynchronize(ctx->stream));
+    if (rowptr && csr->rowptr && first != 0 && dst_on_host)
+        for (int64_t i = 0; i <= csr->nrows; i++) rowptr[i] -= first;
     return RRQ_OK;
 }
 
 extern "C" rrq_status rrq_csr_free(rrq_ctx *ctx, rrq_csr *csr) {
-    if (!ctx || !csr) return RRQ_ERR_ARG;
+    if (!ctx || !csr || (csr->kernel_mask & RRQ_CSR_VIEW)) return RRQ_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     if (csr->rowptr) cudaFreeAsync(csr->rowptr, ctx->stream);
     if (csr->col) cudaFreeAsync(csr->col, ctx->stream);
@@ -502,9 +420,7 @@ __global__ void __launch_bounds__(APPLY_TILE) k_apply(int kernel, const double *
                                                       const double *__restrict__ wts, const double *__restrict__ sig,
                                                       int64_t nnode, const double *__restrict__ txyz,
                                                       const double *__restrict__ tnrm, const int64_t *__restrict__ tself,
-                                                      int64_t ntarg, const int64_t *__restrict__ rowptr,
-                                                      const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                      double *__restrict__ out) {
+                                                      int64_t ntarg, double *__restrict__ out) {
     __shared__ double sx[APPLY_TILE * 3], sn[APPLY_TILE * 3], sw[APPLY_TILE];
     const int64_t t = (int64_t)blockIdx.x * APPLY_TILE + threadIdx.x;
     const bool act = t < ntarg;
@@ -543,12 +459,23 @@ __global__ void __launch_bounds__(APPLY_TILE) k_apply(int kernel, const double *
                 acc += kv * sw[k];
             }
     }
-    if (act) {
-        double c = 0.0;
-        if (val)
-            for (int64_t q = rowptr[t]; q < rowptr[t + 1]; q++) c += val[q] * sig[col[q]];
-        out[t] = acc + c;
-    }
+    if (act) out[t] = acc;
+}
+
+// out[t] += sum_q val[q] sigma[col[q]] over row t: one warp per row, lanes stride the
+// row's entries (coalesced val/col loads; sigma gathers hit L1/L2).  HBM bound: 12 bytes
+// per entry plus the row pointers.
+__global__ void __launch_bounds__(256) k_spmv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                             const double *__restrict__ val, const double *__restrict__ sig,
+                                             int64_t nrows, double *__restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    const int64_t a = rowptr[row], b = rowptr[row + 1];
+    double s = 0.0;
+    for (int64_t q = a + lane; q < b; q += 32) s = fma(__ldcs(val + q), __ldg(sig + __ldcs(col + q)), s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[row] += s;
 }
 
 }  // namespace
@@ -578,14 +505,28 @@ extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq
     if (o.inputs_on_host) d_out = (double *)Scratch::alloc(&s, sizeof(double) * (in.ntarg > 0 ? in.ntarg : 1));
     if (err != cudaSuccess || s.failed) return RRQ_ERR_OOM;
     if (in.ntarg > 0) {
+        CK(cudaEventRecord(ctx->ev[0], s.st));
         k_apply<<<(unsigned)((in.ntarg + APPLY_TILE - 1) / APPLY_TILE), APPLY_TILE, 0, s.st>>>(
-            kernel, in.xyz, in.nrm, in.wts, d_sig, in.nnode, in.txyz, in.tnrm, in.tself, in.ntarg,
-            corr ? corr->rowptr : nullptr, corr ? corr->col : nullptr, val, d_out);
+            kernel, in.xyz, in.nrm, in.wts, d_sig, in.nnode, in.txyz, in.tnrm, in.tself, in.ntarg, d_out);
         CK(cudaGetLastError());
+        CK(cudaEventRecord(ctx->ev[1], s.st));
+        if (val) {
+            k_spmv<<<(unsigned)((in.ntarg * 32 + 255) / 256), 256, 0, s.st>>>(corr->rowptr, corr->col, val, d_sig,
+                                                                              in.ntarg, d_out);
+            CK(cudaGetLastError());
+        }
+        CK(cudaEventRecord(ctx->ev[2], s.st));
     }
     if (o.inputs_on_host && in.ntarg > 0)
         CK(cudaMemcpyAsync(out, d_out, sizeof(double) * in.ntarg, cudaMemcpyDeviceToHost, s.st));
     CK(cudaStreamSynchronize(s.st));
+    if (in.ntarg > 0) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+        ctx->diag.ms_apply_smooth = ms;
+        cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+        ctx->diag.ms_apply_spmv = ms;
+    }
     return RRQ_OK;
 }
 
@@ -688,7 +629,7 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     if (o.inputs_on_host) {
-        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: inputs must be device pointers");
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: inputs must be device pointers");
         return RRQ_ERR_ARG;
     }
     if (ctx->device < 0 || ctx->device >= RRQ_MAX_DEVICES) return RRQ_ERR_ARG;
@@ -743,12 +684,13 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
             CK(cudaMemcpyAsync(tabs[p], &htab[p], sizeof(OrderTables), cudaMemcpyHostToDevice, st));
         }
     const size_t NPc = npatch;
-    PatchData pd;
+    PatchData pd{};
     pd.npatch = npatch;
     pd.pmax = pmax;
     pd.frame = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * PD_FRAME);
     pd.bounds = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * PD_BOUNDS);
     pd.ynode = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ynode());
+    pd.xm = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ynode());
     pd.ea = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ea());
     pd.ey = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey());
     pd.et = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey());
@@ -766,7 +708,7 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     int32_t *d_rank = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);
     BuildCounters *d_cnt = (BuildCounters *)StaticArena::alloc(&ar, sizeof(BuildCounters));
     if (ar.failed) {
-        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
                  ar.wanted, (size_t)RRQ_STATIC_SCRATCH_BYTES);
         return RRQ_ERR_ARG;
     }
@@ -795,7 +737,7 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
         e = rrq_items_build(&nb, ntarg, surf->order, d_rank, npatch, &StaticArena::alloc, &ar, rowptr, &items, &roff, st);
     if (ar.failed) {
         cudaStreamSynchronize(st);
-        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
                  ar.wanted, (size_t)RRQ_STATIC_SCRATCH_BYTES);
         return RRQ_ERR_ARG;
     }
@@ -812,13 +754,14 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     for (int P = 0; P < npatch; P++)
         if (h_status[P]) return RRQ_ERR_DEGENERATE;
     if (nnz > capacity) {
-        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: %lld entries exceed the output capacity %lld",
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: %lld entries exceed the output capacity %lld",
                  (long long)nnz, (long long)capacity);
         return RRQ_ERR_ARG;
     }
     pd.roots = (EdgeRoot *)StaticArena::alloc(&ar, sizeof(EdgeRoot) * 3 * (nb.npairs > 0 ? nb.npairs : 1));
+    pd.uside = (int8_t *)StaticArena::alloc(&ar, sizeof(int8_t) * (nb.npairs > 0 ? nb.npairs : 1));
     if (ar.failed) {
-        snprintf(g_err, sizeof(g_err), "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
                  ar.wanted, (size_t)RRQ_STATIC_SCRATCH_BYTES);
         return RRQ_ERR_ARG;
     }
@@ -830,11 +773,14 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
                 int64_t i0 = h_roff[start], i1 = h_roff[start + n];
                 PatchData pdo = pd;
                 pdo.roots = pd.roots + 3 * i0;
-                CK(rrq_launch_pairs(p, tabs[p], items + i0, i1 - i0, pdo, surf->node_off, surf->xyz, surf->nrm,
-                                    surf->wts, targ->xyz, targ->nrm, targ->self_node, kernel_mask, newton_max,
-                                    (kernel_mask & RRQ_S) ? val[0] : nullptr, (kernel_mask & RRQ_D) ? val[1] : nullptr,
-                                    (kernel_mask & RRQ_SP) ? val[2] : nullptr,
-                                    (kernel_mask & RRQ_DP) ? val[3] : nullptr, col, d_cnt, st));
+                pdo.uside = pd.uside + i0;
+                const PairArgs pa = {tabs[p], items + i0, i1 - i0, pdo, surf->node_off, surf->xyz, surf->nrm,
+                                     surf->wts, targ->xyz, targ->nrm, targ->self_node, kernel_mask, newton_max,
+                                     {(kernel_mask & RRQ_S) ? val[0] : nullptr, (kernel_mask & RRQ_D) ? val[1] : nullptr,
+                                      (kernel_mask & RRQ_SP) ? val[2] : nullptr,
+                                      (kernel_mask & RRQ_DP) ? val[3] : nullptr},
+                                     col, d_cnt};
+                CK(rrq_launch_pairs(p, false, pa, PairShape{0, 0, nullptr}, st));
             }
             start += n;
         }

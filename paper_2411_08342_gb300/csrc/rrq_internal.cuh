@@ -56,6 +56,8 @@ struct OrderTables {
     double dLeg[RRQ_PTMAX * RRQ_PMAX];              // [q][n] P_n'(t_q)
     double LegU[2 * RRQ_PTMAX * RRQ_PMAX];          // [s][n] P_n(tu_s)
     double L2M[RRQ_PMAX * RRQ_PMAX];                // [n][k] coefficient of t^k in P_n(t)
+    double Mmon[RRQ_NPMAX * RRQ_NPMAX];             // [ab][i] coefficient of u^a v^b in the node
+                                                    // Lagrange function l_i (ab a-major, a + b < p)
 };
 
 // Complex preimage of one (pair, edge): Re t0, Im t0, converged (0/1), singularity swap (0/1).
@@ -83,7 +85,10 @@ struct PatchData {
     double *XS2;     // [P][4*NPMAX][NPMAX] quaternion fit of the intermediate density
     double *XS1;     // [P][NPMAX][NPMAX]   scalar fit A_S^{-1}
     int *status;     // [P] 0 ok, nonzero = singular fit / degenerate patch
+    double *xm;      // [P][NPMAX*3] monomial coefficients [ab][a] of the local node interpolant
     EdgeRoot *roots;  // [pair item][3 edges]: (Re t0, Im t0, converged, singularity swap)
+    int8_t *uside;    // [pair item] side of the patch the target is on along e_z (+1, -1), 0 = unknown
+    const int64_t *col_off;  // [P] first CSR column of the patch's nodes, or NULL = node_off
 };
 
 static const size_t PD_FRAME = 16, PD_BOUNDS = 5;
@@ -118,16 +123,30 @@ int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, Orde
 cudaError_t rrq_launch_precompute(int p, const OrderTables *d_tab, const int32_t *d_plist, int n,
                                   const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
                                   PatchData pd, cudaStream_t st);
-cudaError_t rrq_launch_pairs(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems,
-                             PatchData pd, const int64_t *d_node_off, const double *d_xyz,
-                             const double *d_nrm, const double *d_wts, const double *d_txyz,
-                             const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
-                             int newton_max, double *vS, double *vD, double *vSp, double *vDp,
-                             int32_t *col, BuildCounters *cnt, cudaStream_t st);
-// mixed-precision variant (line integrals in double-float; needs pd.eg2, pd.eh2)
-cudaError_t rrq_launch_pairs_mix(int p, const OrderTables *d_tab, const PairItem *d_items, int64_t nitems,
-                                 PatchData pd, const int64_t *d_node_off, const double *d_xyz,
-                                 const double *d_nrm, const double *d_wts, const double *d_txyz,
-                                 const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
-                                 int newton_max, double *vS, double *vD, double *vSp, double *vDp,
-                                 int32_t *col, BuildCounters *cnt, cudaStream_t st);
+// Arguments of the per-pair stage of one order (Sec. 4 Steps 4-8 for every pair item).
+struct PairArgs {
+    const OrderTables *tab;
+    const PairItem *items;
+    int64_t nitems;
+    PatchData pd;
+    const int64_t *node_off;
+    const double *xyz, *nrm, *wts, *txyz, *tnrm;
+    const int64_t *tself;
+    uint32_t mask;
+    int newton_max;
+    double *val[4];       // S, D, S', D' values (NULL = not built)
+    int32_t *col;
+    BuildCounters *cnt;
+};
+
+// Launch shape of the per-pair stage.
+struct PairShape {
+    int tile;                       // pairs per CTA; 0 = the order's default
+    int persistent;                 // 1: one wave of CTAs fetching tiles from tile_ctr; 0: grid-stride over 16 waves
+    unsigned long long *tile_ctr;   // device counter for persistent launches (zeroed by the launcher)
+};
+
+// Roots and pair kernels of order p; mixed = line integrals in double-float (needs pd.eg2, pd.eh2).
+cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape shape, cudaStream_t st);
+// Tile sizes compiled for order p (the first is the default); returns their number.
+int rrq_pair_tiles(int p, int tiles[4]);

@@ -1,20 +1,9 @@
-// Instantiation of the per-pair kernel for patch order p = 3.
+// Instantiation of the per-pair stage for patch order p = 3: tiles of 8, 4 pairs per CTA
+// (the first is the default), FP64 and mixed line integrals.
 #include "rrq_pairs_tile.cuh"
 
-cudaError_t rrq_launch_pairs_p3(const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
-                                 const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
-                                 const double *d_wts, const double *d_txyz, const double *d_tnrm,
-                                 const int64_t *d_tself, uint32_t mask, int newton_max, double *vS, double *vD,
-                                 double *vSp, double *vDp, int32_t *col, BuildCounters *cnt, cudaStream_t st) {
-    return rrqk::launch_pairs_tile<3, false>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts, d_txyz, d_tnrm,
-                                    d_tself, mask, newton_max, vS, vD, vSp, vDp, col, cnt, st);
+cudaError_t rrq_launch_pairs_p3(bool mixed, const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    return rrqk::launch_pairs_order<3, 8, 4>(mixed, a, shape, st);
 }
 
-cudaError_t rrq_launch_pairs_mix_p3(const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
-                                     const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
-                                     const double *d_wts, const double *d_txyz, const double *d_tnrm,
-                                     const int64_t *d_tself, uint32_t mask, int newton_max, double *vS, double *vD,
-                                     double *vSp, double *vDp, int32_t *col, BuildCounters *cnt, cudaStream_t st) {
-    return rrqk::launch_pairs_tile<3, true>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts, d_txyz,
-                                         d_tnrm, d_tself, mask, newton_max, vS, vD, vSp, vDp, col, cnt, st);
-}
+int rrq_pair_tiles_p3(int out[4]) { return rrqk::tiles_of<8, 4>(out); }

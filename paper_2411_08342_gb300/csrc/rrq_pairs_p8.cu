@@ -1,20 +1,9 @@
-// Instantiation of the per-pair kernel for patch order p = 8.
+// Instantiation of the per-pair stage for patch order p = 8: tiles of 4, 2 pairs per CTA
+// (the first is the default), FP64 and mixed line integrals.
 #include "rrq_pairs_tile.cuh"
 
-cudaError_t rrq_launch_pairs_p8(const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
-                                 const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
-                                 const double *d_wts, const double *d_txyz, const double *d_tnrm,
-                                 const int64_t *d_tself, uint32_t mask, int newton_max, double *vS, double *vD,
-                                 double *vSp, double *vDp, int32_t *col, BuildCounters *cnt, cudaStream_t st) {
-    return rrqk::launch_pairs_tile<8, false>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts, d_txyz, d_tnrm,
-                                    d_tself, mask, newton_max, vS, vD, vSp, vDp, col, cnt, st);
+cudaError_t rrq_launch_pairs_p8(bool mixed, const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    return rrqk::launch_pairs_order<8, 4, 2>(mixed, a, shape, st);
 }
 
-cudaError_t rrq_launch_pairs_mix_p8(const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
-                                     const int64_t *d_node_off, const double *d_xyz, const double *d_nrm,
-                                     const double *d_wts, const double *d_txyz, const double *d_tnrm,
-                                     const int64_t *d_tself, uint32_t mask, int newton_max, double *vS, double *vD,
-                                     double *vSp, double *vDp, int32_t *col, BuildCounters *cnt, cudaStream_t st) {
-    return rrqk::launch_pairs_tile<8, true>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts, d_txyz,
-                                         d_tnrm, d_tself, mask, newton_max, vS, vD, vSp, vDp, col, cnt, st);
-}
+int rrq_pair_tiles_p8(int out[4]) { return rrqk::tiles_of<4, 2>(out); }

@@ -12,7 +12,6 @@ namespace rrqk {
 
 template <int P>
 struct TileCfg {
-    static constexpr int T = P <= 4 ? 8 : (P <= 6 ? 6 : 4);  // pairs per CTA
     static constexpr int THREADS = 128;
 };
 
@@ -36,20 +35,27 @@ __device__ __forceinline__ void dfmac(dfa &acc, float ah, float al, float bh, fl
 
 __device__ __forceinline__ double dfval(const dfa &a) { return (double)a.h + (double)a.l; }
 
-template <int P, bool MIX>
-__global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restrict__ tab, const PairItem *__restrict__ items,
-                                                    int64_t nitems, PatchData pd, const int64_t *__restrict__ node_off,
-                                                    const double *__restrict__ xyz, const double *__restrict__ nrm,
-                                                    const double *__restrict__ wts, const double *__restrict__ txyz,
-                                                    const double *__restrict__ tnrm, const int64_t *__restrict__ tself,
-                                                    uint32_t mask, int newton_max, double *vS, double *vD, double *vSp,
-                                                    double *vDp, int32_t *col, BuildCounters *cnt) {
+template <int P, bool MIX, int T>
+__global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned long long *tile_ctr) {
+    const OrderTables *__restrict__ tab = a.tab;
+    const PairItem *__restrict__ items = a.items;
+    const int64_t nitems = a.nitems;
+    const PatchData &pd = a.pd;
+    const int64_t *__restrict__ node_off = a.node_off;
+    const int64_t *__restrict__ col_off = a.pd.col_off ? a.pd.col_off : a.node_off;
+    const double *__restrict__ xyz = a.xyz, *__restrict__ nrm = a.nrm, *__restrict__ wts = a.wts;
+    const double *__restrict__ txyz = a.txyz, *__restrict__ tnrm = a.tnrm;
+    const int64_t *__restrict__ tself = a.tself;
+    const uint32_t mask = a.mask;
+    double *vS = a.val[0], *vD = a.val[1], *vSp = a.val[2], *vDp = a.val[3];
+    int32_t *col = a.col;
+    BuildCounters *cnt = a.cnt;
     using Z = PairSm<P>;
-    constexpr int T = TileCfg<P>::T;
     constexpr int NP = Z::NP, PT = Z::PT, NJK = Z::NJK, NS = Z::NS, NUP = Z::NUP;
     extern __shared__ double smraw[];
     __shared__ unsigned int bc[5];
     __shared__ PairItem s_item[T];
+    __shared__ int64_t s_base;
     __shared__ int s_self[T];
     __shared__ double s_uz[T];
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
@@ -60,9 +66,14 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
                                                3628800.0, 39916800.0, 479001600.0, 6227020800.0, 87178291200.0,
                                                1307674368000.0, 20922789888000.0, 355687428096000.0};
 #define SW(pl) (smraw + (size_t)(pl) * Z::TOTAL)
-    for (int64_t base = (int64_t)blockIdx.x * T; base < nitems; base += (int64_t)gridDim.x * T) {
-        const int nt = (int)min((int64_t)T, nitems - base);
+    // tiles of T consecutive items: grid-stride, or (persistent launch) fetched from a counter
+    for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
         __syncthreads();
+        if (tid == 0) s_base = (tile_ctr ? (int64_t)atomicAdd(tile_ctr, 1ULL) : tile) * T;
+        __syncthreads();
+        const int64_t base = s_base;
+        if (base >= nitems) break;
+        const int nt = (int)min((int64_t)T, nitems - base);
         if (tid < nt) s_item[tid] = items[base + tid];
         __syncthreads();
         // A: frame, target, normal, edge coefficients
@@ -158,9 +169,17 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
         }
         __syncthreads();
         // E: choice of u (warp per pair)
+        // +e_z for a node of the patch (exterior limit); the side the target is on when its
+        // footprint along e_z lies in the patch (k_uside); otherwise the better of +-e_z by
+        // the smallest u.(y'-y)/|y'-y| over nodes and edge samples
         for (int pl = warp; pl < nt; pl += nwarp) {
             double *sw = SW(pl);
             const size_t ps = (size_t)s_item[pl].P;
+            const int side = s_self[pl] < 0 ? pd.uside[base + pl] : 0;
+            if (side != 0) {
+                if (lane == 0) s_uz[pl] = (double)side;
+                continue;
+            }
             const double *yt = sw + Z::YT, *dq = sw + Z::DQ;
             double mplus = 2.0, mminus = 2.0;
             for (int s2 = lane; s2 < NP + NS; s2 += 32) {
@@ -647,7 +666,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const OrderTables *__restric
                 rDp -= wk * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) / r3 - 3.0 * dns * dnt / (r3 * r2));
             }
             const int64_t dst = im.off + i;
-            col[dst] = (int32_t)(o + i);
+            col[dst] = (int32_t)(col_off[im.P] + i);
             if ((mask & RRQ_S) && vS) vS[dst] = rS;
             if ((mask & RRQ_D) && vD) vD[dst] = rD;
             if ((mask & RRQ_SP) && vSp) vSp[dst] = rSp;
@@ -735,34 +754,150 @@ __global__ void __launch_bounds__(128) k_roots(const OrderTables *__restrict__ t
     pd.roots[idx] = EdgeRoot{tt.x, tt.y, (double)conv, (double)ssq};
 }
 
-template <int P, bool MIX>
-cudaError_t launch_pairs_tile(const OrderTables *d_tab, const PairItem *d_items, int64_t nitems, PatchData pd,
-                              const int64_t *d_node_off, const double *d_xyz, const double *d_nrm, const double *d_wts,
-                              const double *d_txyz, const double *d_tnrm, const int64_t *d_tself, uint32_t mask,
-                              int newton_max, double *vS, double *vD, double *vSp, double *vDp, int32_t *col,
-                              BuildCounters *cnt, cudaStream_t st) {
-    constexpr int T = TileCfg<P>::T, NTH = TileCfg<P>::THREADS;
+// Side of patch P on which the target lies along the frame axis e_z, one thread per pair
+// item: Newton for the footprint (u, v) with X_xy(u, v) = y'_xy on the monomial form of
+// the local node interpolant, from the barycentric coordinates of y'_xy in the
+// projected vertex triangle (|du| + |dv| <= 1e-14 (1 + |u| + |v|), 30 steps).  +1 when
+// the footprint lies in the reference triangle (tolerance 1e-12) and y'_z >= X_z(u, v),
+// -1 when below, 0 when outside, not converged, or the target is a node of the patch.
+template <int P>
+__global__ void __launch_bounds__(128) k_uside(const PairItem *__restrict__ items, int64_t nitems, PatchData pd,
+                                               const int64_t *__restrict__ node_off,
+                                               const double *__restrict__ txyz, const int64_t *__restrict__ tself) {
+    constexpr int NP = P * (P + 1) / 2;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nitems) return;
+    const PairItem im = items[n];
+    int8_t side = 0;
+    const int64_t o = node_off[im.P];
+    const bool self = tself && tself[im.t] >= o && tself[im.t] < o + NP;
+    if (!self) {
+        const double *fr = pd.frame + (size_t)im.P * PD_FRAME;
+        double yt[3];
+        for (int b = 0; b < 3; b++) {
+            double sy = 0;
+            for (int a = 0; a < 3; a++) sy += fr[3 + 3 * a + b] * (txyz[3 * im.t + a] - fr[a]);
+            yt[b] = fr[12] * sy;
+        }
+        const double *xm = pd.xm + (size_t)im.P * pd_ynode();
+        // vertices X(0,0) = xm[00], X(1,0) = sum_a xm[a0], X(0,1) = sum_b xm[0b]
+        double v0[2] = {xm[0], xm[1]}, v1[2] = {0, 0}, v2[2] = {0, 0};
+        {
+            int ab = 0;
+            for (int a = 0; a < P; a++)
+                for (int b = 0; a + b < P; b++, ab++) {
+                    if (b == 0) { v1[0] += xm[3 * ab]; v1[1] += xm[3 * ab + 1]; }
+                    if (a == 0) { v2[0] += xm[3 * ab]; v2[1] += xm[3 * ab + 1]; }
+                }
+        }
+        const double a11 = v1[0] - v0[0], a12 = v2[0] - v0[0], a21 = v1[1] - v0[1], a22 = v2[1] - v0[1];
+        const double det = a11 * a22 - a12 * a21;
+        if (det != 0.0) {
+            const double rx = yt[0] - v0[0], ry = yt[1] - v0[1];
+            double u = (a22 * rx - a12 * ry) / det, v = (a11 * ry - a21 * rx) / det;
+            bool conv = false;
+            for (int it = 0; it < 30; it++) {
+                // X_xy and its derivatives at (u, v): powers by recurrence
+                double X0 = 0, X1 = 0, Xu0 = 0, Xu1 = 0, Xv0 = 0, Xv1 = 0;
+                double ua = 1.0, ua1 = 0.0;  // u^a, a u^(a-1)
+                int ab = 0;
+                for (int a = 0; a < P; a++) {
+                    double vb = 1.0, vb1 = 0.0;  // v^b, b v^(b-1)
+                    for (int b = 0; a + b < P; b++, ab++) {
+                        const double c0 = xm[3 * ab], c1 = xm[3 * ab + 1];
+                        const double m = ua * vb, mu = ua1 * vb, mv = ua * vb1;
+                        X0 = fma(c0, m, X0); X1 = fma(c1, m, X1);
+                        Xu0 = fma(c0, mu, Xu0); Xu1 = fma(c1, mu, Xu1);
+                        Xv0 = fma(c0, mv, Xv0); Xv1 = fma(c1, mv, Xv1);
+                        vb1 = vb * (b + 1);
+                        vb *= v;
+                    }
+                    ua1 = ua * (a + 1);
+                    ua *= u;
+                }
+                const double dj = Xu0 * Xv1 - Xv0 * Xu1;
+                if (dj == 0.0) break;
+                const double fx = X0 - yt[0], fy = X1 - yt[1];
+                const double du = (Xv1 * fx - Xv0 * fy) / dj, dv = (Xu0 * fy - Xu1 * fx) / dj;
+                u -= du;
+                v -= dv;
+                if (fabs(du) + fabs(dv) <= 1e-14 * (1.0 + fabs(u) + fabs(v))) { conv = true; break; }
+            }
+            const double tol = 1e-12;
+            if (conv && u >= -tol && v >= -tol && u + v <= 1.0 + tol) {
+                double Xz = 0.0, ua = 1.0;
+                int ab = 0;
+                for (int a = 0; a < P; a++) {
+                    double vb = 1.0;
+                    for (int b = 0; a + b < P; b++, ab++) {
+                        Xz = fma(xm[3 * ab + 2], ua * vb, Xz);
+                        vb *= v;
+                    }
+                    ua *= u;
+                }
+                side = yt[2] >= Xz ? 1 : -1;
+            }
+        }
+    }
+    pd.uside[n] = side;
+}
+
+template <int P, bool MIX, int T>
+cudaError_t launch_pairs_tile(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    constexpr int NTH = TileCfg<P>::THREADS;
     const size_t bytes = sizeof(double) * PairSm<P>::TOTAL * T;
-    cudaError_t e = cudaFuncSetAttribute(k_pairs_tile<P, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_pairs_tile<P, MIX, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    if (nitems <= 0) return cudaSuccess;
+    if (a.nitems <= 0) return cudaSuccess;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX>, NTH, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX, T>, NTH, bytes);
     if (per_sm < 1) per_sm = 1;
-    k_roots<P><<<(unsigned)((nitems * 3 + 127) / 128), 128, 0, st>>>(d_tab, d_items, nitems, pd, d_txyz, newton_max);
+    k_roots<P><<<(unsigned)((a.nitems * 3 + 127) / 128), 128, 0, st>>>(a.tab, a.items, a.nitems, a.pd, a.txyz,
+                                                                       a.newton_max);
     RRQ_COUNT_LAUNCH();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int64_t want = (nitems + T - 1) / T;
-    int64_t grid = (int64_t)nsm * per_sm * 16;
+    k_uside<P><<<(unsigned)((a.nitems + 127) / 128), 128, 0, st>>>(a.items, a.nitems, a.pd, a.node_off, a.txyz,
+                                                                   a.tself);
+    RRQ_COUNT_LAUNCH();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t want = (a.nitems + T - 1) / T;
+    int64_t grid = (int64_t)nsm * per_sm * (shape.persistent ? 1 : 16);
     if (grid > want) grid = want;
-    k_pairs_tile<P, MIX><<<(unsigned)grid, NTH, bytes, st>>>(d_tab, d_items, nitems, pd, d_node_off, d_xyz, d_nrm, d_wts,
-                                                        d_txyz, d_tnrm, d_tself, mask, newton_max, vS, vD, vSp, vDp,
-                                                        col, cnt);
+    unsigned long long *ctr = shape.persistent ? shape.tile_ctr : nullptr;
+    if (shape.persistent) {
+        if (!ctr) return cudaErrorInvalidValue;
+        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_pairs_tile<P, MIX, T><<<(unsigned)grid, NTH, bytes, st>>>(a, ctr);
     RRQ_COUNT_LAUNCH();
     return cudaGetLastError();
+}
+
+// Dispatch on the tile size among the compiled ones (Ts, the first being the default).
+template <int P, int... Ts>
+cudaError_t launch_pairs_order(bool mixed, const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    constexpr int tiles[] = {Ts...};
+    const int T = shape.tile ? shape.tile : tiles[0];
+    cudaError_t e = cudaErrorInvalidValue;
+    ((T == Ts ? (void)(e = mixed ? launch_pairs_tile<P, true, Ts>(a, shape, st)
+                                 : launch_pairs_tile<P, false, Ts>(a, shape, st))
+              : (void)0),
+     ...);
+    return e;
+}
+
+template <int... Ts>
+int tiles_of(int out[4]) {
+    constexpr int tiles[] = {Ts...};
+    int n = 0;
+    for (int t : tiles)
+        if (n < 4) out[n++] = t;
+    return n;
 }
 
 }  // namespace rrqk

@@ -235,6 +235,14 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
     for (int w = tid; w < 9 * P; w += nth) g_ea[w] = sea[w];
     for (int w = tid; w < 9 * PT; w += nth) g_ey[w] = sey[w];
     for (int w = tid; w < 3 * NP; w += nth) g_yn[w] = syn[w];
+    // monomial coefficients of the local node interpolant X(u, v) = sum_ab xm[ab] u^a v^b
+    double *g_xm = pd.xm + (size_t)pid * pd_ynode();
+    for (int w = tid; w < 3 * NP; w += nth) {
+        const int ab = w / 3, a = w % 3;
+        double v = 0.0;
+        for (int i = 0; i < NP; i++) v = fma(tab->Mmon[ab * NP + i], syn[3 * i + a], v);
+        g_xm[w] = v;
+    }
     for (int w = tid; w < 3 * PT * 3; w += nth) {
         int q = w / 3, a = w % 3, e = q / PT, qq = q % PT;
         double s = 0;

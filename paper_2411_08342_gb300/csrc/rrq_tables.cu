@@ -218,5 +218,18 @@ int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, Orde
             if (k > 0) v += (2.0 * n + 1.0) * T->L2M[n * p + k - 1];
             T->L2M[(n + 1) * p + k] = v / (n + 1.0);
         }
+    // monomial coefficients of the node Lagrange functions: Vm[i][ab] = u_i^a v_i^b, Mmon = Vm^{-1}
+    {
+        std::vector<double> Vm(np * np), I(np * np, 0.0);
+        for (int i = 0; i < np; i++) {
+            int ab = 0;
+            for (int a = 0; a < p; a++)
+                for (int b = 0; a + b < p; b++, ab++)
+                    Vm[i * np + ab] = pow(ref_uv[2 * i], a) * pow(ref_uv[2 * i + 1], b);
+            I[i * np + i] = 1.0;
+        }
+        if (solve_complete_pivot(np, Vm, np, I)) return -2;
+        for (int i = 0; i < np * np; i++) T->Mmon[i] = I[i];
+    }
     return 0;
 }

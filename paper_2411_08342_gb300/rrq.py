@@ -45,7 +45,19 @@ class CSR(C.Structure):
 class Diag(C.Structure):
     _fields_ = [("npairs", C.c_int64), ("newton_fail", C.c_int64), ("on_edge", C.c_int64), ("u_poor", C.c_int64),
                 ("ssq_edges", C.c_int64), ("far_edges", C.c_int64), ("ms_near", C.c_double),
-                ("ms_precompute", C.c_double), ("ms_pairs", C.c_double), ("kernel_launches", C.c_int64)]
+                ("ms_precompute", C.c_double), ("ms_pairs", C.c_double), ("kernel_launches", C.c_int64),
+                ("ms_apply_smooth", C.c_double), ("ms_apply_spmv", C.c_double)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("nsurf", C.c_int32), ("nrows", C.c_int64), ("nnode", C.c_int64), ("nnz", C.c_int64),
+                ("npairs", C.c_int64), ("graph_kernels", C.c_int32), ("tile", C.c_int32 * (PMAX + 1)),
+                ("persistent", C.c_int32 * (PMAX + 1)), ("ms_create", C.c_double), ("ms_autotune", C.c_double),
+                ("ms_last_execute", C.c_double)]
+
+
+BATCH_AUTOTUNE = 1
+CSR_VIEW = 0x80000000
 
 
 class RRQError(RuntimeError):
@@ -81,6 +93,12 @@ def load(build_if_needed: bool = True):
                                                        C.c_uint32, C.POINTER(Options), C.c_void_p, C.c_void_p,
                                                        C.c_void_p * 4, C.c_int64, C.POINTER(C.c_int64),
                                                        C.POINTER(C.c_int64)]
+            L.rrq_batch_create.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Surface), C.POINTER(TargetsS),
+                                           C.c_uint32, C.POINTER(Options), C.c_uint32, C.POINTER(C.c_void_p)]
+            L.rrq_batch_execute.argtypes = [C.c_void_p, C.c_void_p]
+            L.rrq_batch_csr.argtypes = [C.c_void_p, C.c_int32, C.POINTER(CSR), C.c_void_p, C.c_void_p]
+            L.rrq_batch_info_get.argtypes = [C.c_void_p, C.POINTER(BatchInfo)]
+            L.rrq_batch_destroy.argtypes = [C.c_void_p]
             _lib = L
     return _lib
 
@@ -181,6 +199,11 @@ class Context:
         _check(st, "rrq_build_corrections_static")
         return nnz.value, npairs.value
 
+    def batch(self, surfs, targs, kernels=("S", "D", "SP", "DP"), mixed: bool = False, autotune: bool = False,
+              inputs_on_host: bool = False) -> "Batch":
+        """Batch plan over several surfaces (rrq_batch_create); see Batch."""
+        return Batch(self, surfs, targs, kernels, mixed, autotune, inputs_on_host)
+
     def csr_free(self, csr: CSR):
         _check(self.L.rrq_csr_free(self.h, C.byref(csr)), "rrq_csr_free")
 
@@ -237,3 +260,59 @@ def device_inputs(disc, targets, device="cuda"):
                 xyz=t(disc.xyz, torch.float64), nrm=t(disc.nrm, torch.float64), wts=t(disc.wts, torch.float64),
                 txyz=t(targets.xyz, torch.float64), tnrm=t(targets.nrm, torch.float64),
                 tself=t(targets.self_node, torch.int64))
+
+
+class Batch:
+    """Many surfaces built together: rrq_batch_create at construction, execute() launches
+    the recorded graph, view(s) is the CSR of surface s (columns local to that surface)."""
+
+    def __init__(self, ctx: Context, surfs, targs, kernels, mixed, autotune, inputs_on_host):
+        self.ctx, self.L = ctx, ctx.L
+        n = len(surfs)
+        if n != len(targs) or n < 1:
+            raise RRQError("one targets set per surface is required")
+        self._surfs = (Surface * n)(*surfs)
+        self._targs = (TargetsS * n)(*targs)
+        self._keep = (list(surfs), list(targs))
+        mask = 0
+        for k in kernels:
+            mask |= KERNEL_BITS[k]
+        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, int(mixed))
+        self.h = C.c_void_p()
+        _check(self.L.rrq_batch_create(ctx.h, n, self._surfs, self._targs, mask, C.byref(opt),
+                                       BATCH_AUTOTUNE if autotune else 0, C.byref(self.h)), "rrq_batch_create")
+        self.nsurf = n
+        self.row_start = np.zeros(n + 1, np.int64)
+        self.node_start = np.zeros(n + 1, np.int64)
+        whole = CSR()
+        _check(self.L.rrq_batch_csr(self.h, -1, C.byref(whole), self.row_start.ctypes.data,
+                                    self.node_start.ctypes.data), "rrq_batch_csr")
+        self.csr = whole
+
+    def execute(self) -> int:
+        st = self.L.rrq_batch_execute(self.ctx.h, self.h)
+        return _check(st, "rrq_batch_execute")
+
+    def view(self, s: int) -> CSR:
+        v = CSR()
+        _check(self.L.rrq_batch_csr(self.h, s, C.byref(v), None, None), "rrq_batch_csr")
+        return v
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(self.L.rrq_batch_info_get(self.h, C.byref(i)), "rrq_batch_info_get")
+        d = {f: getattr(i, f) for f, _ in BatchInfo._fields_}
+        d["tile"] = list(i.tile)
+        d["persistent"] = list(i.persistent)
+        return d
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.rrq_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -407,3 +407,30 @@ def wavy_torus(p: int = 8, n_theta: int = 64, n_phi: int = 160, noff: int = 200_
 def ellipsoid81920(p: int = 6, levels: int = 6):
     d = discretize(ellipsoid_surface(levels), p)
     return d, on_surface_targets(d)
+
+
+def random_star_terms(rng, lmin: int = 2, lmax: int = 6, amp: float = 0.25):
+    """Terms (l, m, a) of r = 1 + sum a Re Y_l^m, lmin <= l <= lmax, 0 <= m <= l, with
+    a ~ N(0,1) rescaled so that the largest |perturbation| on a 64 x 128 (theta, phi)
+    grid is amp."""
+    terms = [(l, m, rng.standard_normal()) for l in range(lmin, lmax + 1) for m in range(l + 1)]
+    th, ph = np.meshgrid(np.linspace(0, np.pi, 64), np.linspace(0, 2 * np.pi, 128, endpoint=False), indexing="ij")
+    xh = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1)
+    pert = sum(a * real_ylm(l, m, xh, "re") for (l, m, a) in terms)
+    s = amp / np.abs(pert).max()
+    return [(l, m, a * s) for (l, m, a) in terms]
+
+
+def star_batch(nsurf: int = 64, levels=(1, 2, 3, 4), orders=(4, 6, 8), seed: int = WORKLOAD_SEED + 4):
+    """Batched workload: nsurf star surfaces with seeded random perturbations (max 0.25),
+    each on an icosahedral mesh of 20 * 4^L patches with L drawn from `levels` and an
+    order drawn from `orders`; targets are the on-surface nodes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nsurf):
+        L = int(rng.choice(levels))
+        p = int(rng.choice(orders))
+        terms = random_star_terms(rng)
+        d = discretize(star_surface(L, terms=tuple(terms)), p)
+        out.append((d, on_surface_targets(d)))
+    return out
