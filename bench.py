@@ -172,6 +172,15 @@ def bench_gpu(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    # one-time autotuning of the per-pair launch shapes on this problem (kept in the context)
+    tuned = {}
+    for m in (False, True):
+        b = ctx.batch([surf], [targ], KERNELS, mixed=m, autotune=True)
+        info = b.info()
+        b.close()
+        tuned["mixed" if m else "fp64"] = {"tile": info["tile"][P], "persistent": info["persistent"][P],
+                                           "ms_autotune": info["ms_autotune"]}
+
     def step(mixed=False):
         csr = ctx.build_corrections(surf, targ, KERNELS, mixed=mixed)
         nnz, npairs = csr.nnz, csr.npairs
@@ -252,6 +261,7 @@ def bench_gpu(args):
                      "peak_note": "measured FP64 FMA peak (rrq_measure_fma_peak); FP32 FMA peak %.1f TFLOP/s" % peak32,
                      "flops_per_pair": fpp, "kernel_ms": pair_s * 1e3},
         "stage_ms": {"precompute": diag["ms_precompute"], "near_and_items": diag["ms_near"], "pairs": diag["ms_pairs"]},
+        "launch_shape": tuned,
         "clocks": clk,
         "gpu_launches": launches * args.steps if launches is not None else None,
         "points_per_s": world * tg.n / (ms_step * 1e-3),
@@ -286,7 +296,8 @@ def apply_leg(ctx, surf, targ, d, tg, dev, reps: int = 3) -> dict:
     sig = torch.as_tensor(np.random.default_rng(SEED + 7).standard_normal(d.nnode), dtype=torch.float64,
                           device=dev)
     out = torch.empty(tg.n, dtype=torch.float64, device=dev)
-    spmv, smooth = [], []
+    out32 = torch.empty_like(out)
+    spmv, smooth, smooth32, spmv32, rel32 = [], [], [], [], []
     for k in KERNELS:
         for it in range(reps + 1):
             ctx.apply(surf, targ, k, csr, sig, out)
@@ -294,9 +305,17 @@ def apply_leg(ctx, surf, targ, d, tg, dev, reps: int = 3) -> dict:
             if it > 0:
                 spmv.append(dg["ms_apply_spmv"])
                 smooth.append(dg["ms_apply_smooth"])
+        for it in range(reps + 1):
+            ctx.apply(surf, targ, k, csr, sig, out32, mixed=True)
+            if it > 0:
+                dg = ctx.diagnostics()
+                smooth32.append(dg["ms_apply_smooth"])
+                spmv32.append(dg["ms_apply_spmv"])
+        rel32.append(float((out32 - out).abs().max() / out.abs().max()))
     ctx.csr_free(csr)
     ms_spmv = statistics.median(spmv)
     ms_smooth = statistics.median(smooth)
+    ms_smooth32 = statistics.median(smooth32)
     # algorithmic bytes of one SpMV: val (8) + col (4) per entry, rowptr, out read + write, sigma
     spmv_bytes = nnz * 12 + (tg.n + 1) * 8 + tg.n * 16 + d.nnode * 8
     peak = measured_peaks().get("hbm_gbs")
@@ -304,7 +323,13 @@ def apply_leg(ctx, surf, targ, d, tg, dev, reps: int = 3) -> dict:
     return {"spmv": {"ms": ms_spmv, "nnz": nnz, "bytes": spmv_bytes, "achieved_gbs": gbs, "peak_gbs": peak,
                      "frac": gbs / peak if peak else None, "peak_note": "of measured HBM copy bandwidth"},
             "direct_sum": {"ms": ms_smooth, "interactions_per_s": tg.n * d.nnode / (ms_smooth * 1e-3),
-                           "note": "dense smooth rule over all N_T x N_S pairs (the paper uses an FMM here)"}}
+                           "note": "dense smooth rule over all N_T x N_S pairs (the paper uses an FMM here)"},
+            "apply_mixed": {"ms_far_fp32": ms_smooth32, "ms_spmv_near_fp64": statistics.median(spmv32),
+                            "interactions_per_s": tg.n * d.nnode / ((ms_smooth32 + statistics.median(spmv32)) * 1e-3),
+                            "speedup_vs_fp64": (ms_smooth + ms_spmv) / (ms_smooth32 + statistics.median(spmv32)),
+                            "max_rel_diff_vs_fp64_apply": max(rel32),
+                            "precision": "smooth terms beyond r_c in FP32 (hi/lo coordinates, compensated tile "
+                                         "sums), closer ones in FP64 inside the correction SpMV"}}
 
 
 def batched_leg(ctx, dev) -> dict:

@@ -156,7 +156,10 @@ rrq_status rrq_csr_free(rrq_ctx *ctx, rrq_csr *csr);
  *   out[t] = sum_{j : x_j != target t} K(x_t, x_j) w_j density[j] + sum_j C[t][j] density[j]
  * with K the kernel `kernel` (one of RRQ_S, RRQ_D, RRQ_SP, RRQ_DP) and C its correction
  * CSR.  density [nnode] and out [ntarg] follow inputs_on_host.  The smooth sum is a
- * direct O(ntarg * nnode) sum (no fast multipole method). */
+ * direct O(ntarg * nnode) sum (no fast multipole method); with rrq_options.precision = 1
+ * it runs in FP32 (coordinates as (hi, lo) FP32 pairs so that x_t - x_j keeps ~1e-7
+ * relative accuracy, kernel values in FP32, compensated FP32 sums per tile of 256
+ * sources, FP64 across tiles), the correction SpMV stays FP64. */
 rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, int32_t kernel,
                      const rrq_csr *corr, const double *density, double *out, const rrq_options *opt);
 
@@ -247,6 +250,16 @@ rrq_status rrq_batch_csr(const rrq_batch *batch, int32_t surf, rrq_csr *view, in
                          int64_t *node_start);
 rrq_status rrq_batch_info_get(const rrq_batch *batch, rrq_batch_info *info);
 void rrq_batch_destroy(rrq_batch *batch);
+
+/* Autotune the per-pair stage for this problem (no counterpart in the paper): times every
+ * compiled tile size and both schedules of every order present on a sample of the
+ * problem's pairs (as rrq_batch_create with RRQ_BATCH_AUTOTUNE on one surface) and keeps
+ * the fastest shape per order and precision (rrq_options.precision) in the context;
+ * later rrq_build_corrections calls on this context launch with those shapes.  The
+ * computed values do not depend on the shape.  A batch created with RRQ_BATCH_AUTOTUNE
+ * stores its measured shapes the same way.  Synchronises the context stream. */
+rrq_status rrq_autotune(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, uint32_t kernel_mask,
+                        const rrq_options *opt);
 
 /* Measured fused-multiply-add throughput of this device in TFLOP/s (2 flops per FMA),
  * FP64 (fp32 = 0) or FP32 (fp32 = 1): 8 independent dependency chains per thread,

@@ -142,6 +142,8 @@ rrq_status rrq_ctx_create(rrq_ctx **ctx, int device, void *cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
     memset(&c->diag, 0, sizeof(c->diag));
     for (int p = 0; p <= RRQ_PMAX; p++) { c->d_tab[p] = nullptr; c->tab_rho0[p] = -1; }
+    memset(c->tune_tile, 0, sizeof(c->tune_tile));
+    memset(c->tune_pers, 0, sizeof(c->tune_pers));
     for (int i = 0; i < 4; i++) cudaEventCreate(&c->ev[i]);
     // keep freed stream-ordered memory in the pool between builds
     cudaMemPool_t pool;
@@ -301,7 +303,8 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     }
     EdgeRoot *roots = (EdgeRoot *)Scratch::alloc(&s, sizeof(EdgeRoot) * 3 * (nb.npairs > 0 ? nb.npairs : 1));
     int8_t *uside = (int8_t *)Scratch::alloc(&s, sizeof(int8_t) * (nb.npairs > 0 ? nb.npairs : 1));
-    if (!roots || !uside) oom = true;
+    unsigned long long *tile_ctr = (unsigned long long *)Scratch::alloc(&s, sizeof(unsigned long long) * (RRQ_PMAX + 1));
+    if (!roots || !uside || !tile_ctr) oom = true;
     if (oom) {
         cudaFreeAsync(d_rowptr, s.st);
         cudaFreeAsync(col, s.st);
@@ -321,7 +324,8 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
                 const PairArgs pa = {ctx->d_tab[p], items + i0, i1 - i0, pdo, in.node_off, in.xyz, in.nrm, in.wts,
                                      in.txyz, in.tnrm, in.tself, kernel_mask, newton_max,
                                      {vals[0], vals[1], vals[2], vals[3]}, col, d_cnt};
-                e = rrq_launch_pairs(p, mixed, pa, PairShape{0, 0, nullptr}, s.st);
+                const PairShape shape{ctx->tune_tile[mixed][p], ctx->tune_pers[mixed][p], tile_ctr + p};
+                e = rrq_launch_pairs(p, mixed, pa, shape, s.st);
                 if (e != cudaSuccess) break;
             }
             start += n;
@@ -462,6 +466,148 @@ __global__ void __launch_bounds__(APPLY_TILE) k_apply(int kernel, const double *
     if (act) out[t] = acc;
 }
 
+// Mixed-precision apply.  The smooth sum is split at the distance r_c = eta x (smallest
+// spread of the nodes of one patch): every node closer than r_c to a target belongs to
+// one of the target's near patches (|x_t - c_P| <= |x_t - x_j| + R_P <= R_P + eta d_P),
+// hence to its CSR row.  Terms with |x_t - x_j| >= r_c are summed in FP32 over all
+// sources (k_apply_f32); terms with |x_t - x_j| < r_c -- the large, ill-conditioned ones
+// that the correction cancels -- are added in FP64 by the SpMV over the row
+// (k_spmv_near64).  Both kernels decide "< r_c" by the same FP32 computation
+// (split_r2), so every source is counted exactly once.
+
+// x as a (hi, lo) FP32 pair
+__device__ __forceinline__ void split2(double x, float &h, float &l) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+}
+
+// |x_t - x_j|^2 in FP32 from (hi, lo) pairs; the differences of the hi parts are exact
+// for close points, so close distances keep ~1e-7 relative accuracy
+__device__ __forceinline__ float split_r2(const float th[3], const float tl[3], const float sh[3], const float sl[3],
+                                          float d[3]) {
+    for (int a = 0; a < 3; a++) d[a] = (th[a] - sh[a]) + (tl[a] - sl[a]);
+    return fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+}
+
+// smallest spread (largest node-to-node distance) over the patches, as ordered bits
+__global__ void k_patch_spread(const int64_t *__restrict__ node_off, int npatch, const double *__restrict__ xyz,
+                               unsigned long long *__restrict__ out) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= npatch) return;
+    const int64_t a = node_off[P], b = node_off[P + 1];
+    double m = 0.0;
+    for (int64_t i = a; i < b; i++)
+        for (int64_t k = i + 1; k < b; k++) {
+            const double d0 = xyz[3 * i] - xyz[3 * k], d1 = xyz[3 * i + 1] - xyz[3 * k + 1], d2 = xyz[3 * i + 2] - xyz[3 * k + 2];
+            m = fmax(m, d0 * d0 + d1 * d1 + d2 * d2);
+        }
+    atomicMin(out, (unsigned long long)__double_as_longlong(sqrt(m)));
+}
+
+__global__ void __launch_bounds__(APPLY_TILE) k_apply_f32(int kernel, const double *__restrict__ xyz,
+                                                          const double *__restrict__ nrm,
+                                                          const double *__restrict__ wts, const double *__restrict__ sig,
+                                                          int64_t nnode, const double *__restrict__ txyz,
+                                                          const double *__restrict__ tnrm, int64_t ntarg, float rc2,
+                                                          double *__restrict__ out) {
+    __shared__ float sxh[APPLY_TILE * 3], sxl[APPLY_TILE * 3], sn[APPLY_TILE * 3], sw[APPLY_TILE];
+    const int64_t t = (int64_t)blockIdx.x * APPLY_TILE + threadIdx.x;
+    const bool act = t < ntarg;
+    float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0}, m[3] = {0, 0, 0};
+    if (act)
+        for (int a = 0; a < 3; a++) {
+            split2(txyz[3 * t + a], th[a], tl[a]);
+            m[a] = __double2float_rn(tnrm[3 * t + a]);
+        }
+    const double inv4pi = 0.07957747154594767;
+    double acc = 0.0;
+    for (int64_t base = 0; base < nnode; base += APPLY_TILE) {
+        __syncthreads();
+        const int64_t j = base + threadIdx.x;
+        if (j < nnode) {
+            for (int a = 0; a < 3; a++) {
+                split2(xyz[3 * j + a], sxh[3 * threadIdx.x + a], sxl[3 * threadIdx.x + a]);
+                sn[3 * threadIdx.x + a] = __double2float_rn(nrm[3 * j + a]);
+            }
+            sw[threadIdx.x] = __double2float_rn(wts[j] * sig[j] * inv4pi);
+        }
+        __syncthreads();
+        const int nt = (int)min((int64_t)APPLY_TILE, nnode - base);
+        if (act) {
+            float s = 0.0f, c = 0.0f;
+            for (int k = 0; k < nt; k++) {
+                float d[3];
+                const float r2 = split_r2(th, tl, sxh + 3 * k, sxl + 3 * k, d);
+                const float ri = rsqrtf(r2), ri2 = ri * ri, ri3 = ri2 * ri;
+                float kv;
+                if (kernel == RRQ_S) kv = ri;
+                else if (kernel == RRQ_D) kv = fmaf(d[0], sn[3 * k], fmaf(d[1], sn[3 * k + 1], d[2] * sn[3 * k + 2])) * ri3;
+                else if (kernel == RRQ_SP) kv = -fmaf(d[0], m[0], fmaf(d[1], m[1], d[2] * m[2])) * ri3;
+                else {
+                    const float dn = fmaf(d[0], sn[3 * k], fmaf(d[1], sn[3 * k + 1], d[2] * sn[3 * k + 2]));
+                    const float dm = fmaf(d[0], m[0], fmaf(d[1], m[1], d[2] * m[2]));
+                    kv = fmaf(m[0], sn[3 * k], fmaf(m[1], sn[3 * k + 1], m[2] * sn[3 * k + 2])) * ri3 - 3.0f * dn * dm * ri3 * ri2;
+                }
+                const float term = r2 < rc2 ? 0.0f : kv * sw[k];  // close sources: FP64 in the SpMV
+                // Kahan step: s + c holds the tile's sum
+                const float y = term - c;
+                const float tt = s + y;
+                c = (tt - s) - y;
+                s = tt;
+            }
+            acc += (double)s - (double)c;
+        }
+    }
+    if (act) out[t] = acc;
+}
+
+// out[t] += sum_q val[q] sigma[col[q]] + (smooth terms of the row's nodes closer than r_c,
+// in FP64): one warp per row, as k_spmv plus a gather of the node positions
+__global__ void __launch_bounds__(256) k_spmv_near64(int kernel, const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                     const double *__restrict__ sig, const double *__restrict__ xyz,
+                                                     const double *__restrict__ nrm, const double *__restrict__ wts,
+                                                     const double *__restrict__ txyz, const double *__restrict__ tnrm,
+                                                     const int64_t *__restrict__ tself, float rc2, int64_t nrows,
+                                                     double *__restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    const int64_t a = rowptr[row], b = rowptr[row + 1];
+    const double x0 = txyz[3 * row], x1 = txyz[3 * row + 1], x2 = txyz[3 * row + 2];
+    const double m0 = tnrm[3 * row], m1 = tnrm[3 * row + 1], m2 = tnrm[3 * row + 2];
+    const int64_t self = tself ? tself[row] : -1;
+    float th[3], tl[3];
+    split2(x0, th[0], tl[0]);
+    split2(x1, th[1], tl[1]);
+    split2(x2, th[2], tl[2]);
+    const double inv4pi = 0.07957747154594767;
+    double s = 0.0;
+    for (int64_t q = a + lane; q < b; q += 32) {
+        const int32_t j = __ldcs(col + q);
+        const double sj = __ldg(sig + j);
+        s = fma(__ldcs(val + q), sj, s);
+        if (j == self) continue;
+        float sh[3], sl[3], d[3];
+        for (int c = 0; c < 3; c++) split2(__ldg(xyz + 3 * j + c), sh[c], sl[c]);
+        if (split_r2(th, tl, sh, sl, d) >= rc2) continue;
+        const double d0 = x0 - xyz[3 * j], d1 = x1 - xyz[3 * j + 1], d2 = x2 - xyz[3 * j + 2];
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2, ri = rsqrt(r2), ri2 = ri * ri, ri3 = ri2 * ri;
+        const double n0 = nrm[3 * j], n1 = nrm[3 * j + 1], n2 = nrm[3 * j + 2];
+        double kv;
+        if (kernel == RRQ_S) kv = ri;
+        else if (kernel == RRQ_D) kv = (d0 * n0 + d1 * n1 + d2 * n2) * ri3;
+        else if (kernel == RRQ_SP) kv = -(d0 * m0 + d1 * m1 + d2 * m2) * ri3;
+        else {
+            const double dn = d0 * n0 + d1 * n1 + d2 * n2, dm = d0 * m0 + d1 * m1 + d2 * m2;
+            kv = (m0 * n0 + m1 * n1 + m2 * n2) * ri3 - 3.0 * dn * dm * ri3 * ri2;
+        }
+        s = fma(kv, wts[j] * sj * inv4pi, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[row] += s;
+}
+
 // out[t] += sum_q val[q] sigma[col[q]] over row t: one warp per row, lanes stride the
 // row's entries (coalesced val/col loads; sigma gathers hit L1/L2).  HBM bound: 12 bytes
 // per entry plus the row pointers.
@@ -487,6 +633,7 @@ extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq
     rrq_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
+    if (o.precision != 0 && o.precision != 1) return RRQ_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     Scratch s;
     s.st = ctx->stream;
@@ -504,17 +651,46 @@ extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq
     double *d_out = out;
     if (o.inputs_on_host) d_out = (double *)Scratch::alloc(&s, sizeof(double) * (in.ntarg > 0 ? in.ntarg : 1));
     if (err != cudaSuccess || s.failed) return RRQ_ERR_OOM;
+    const bool mixed = o.precision == 1;
+    if (mixed && !val) {
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_apply: precision = 1 needs the correction CSR");
+        return RRQ_ERR_ARG;
+    }
+    float rc2 = 0.0f;
+    if (mixed && in.ntarg > 0) {
+        // r_c = eta x the smallest node spread of a patch
+        unsigned long long *red = (unsigned long long *)Scratch::alloc(&s, sizeof(unsigned long long));
+        if (!red) return RRQ_ERR_OOM;
+        const unsigned long long init = 0x7FF0000000000000ULL;  // +inf
+        CK(cudaMemcpyAsync(red, &init, sizeof(init), cudaMemcpyHostToDevice, s.st));
+        k_patch_spread<<<(unsigned)((in.npatch + 127) / 128), 128, 0, s.st>>>(in.node_off, in.npatch, in.xyz, red);
+        CK(cudaGetLastError());
+        unsigned long long h = 0;
+        CK(cudaMemcpyAsync(&h, red, sizeof(h), cudaMemcpyDeviceToHost, s.st));
+        CK(cudaStreamSynchronize(s.st));
+        double rc;
+        memcpy(&rc, &h, sizeof(rc));
+        rc *= (o.eta > 0 ? o.eta : 1.0);
+        rc2 = (float)(rc * rc);
+    }
     if (in.ntarg > 0) {
         CK(cudaEventRecord(ctx->ev[0], s.st));
-        k_apply<<<(unsigned)((in.ntarg + APPLY_TILE - 1) / APPLY_TILE), APPLY_TILE, 0, s.st>>>(
-            kernel, in.xyz, in.nrm, in.wts, d_sig, in.nnode, in.txyz, in.tnrm, in.tself, in.ntarg, d_out);
+        if (mixed)
+            k_apply_f32<<<(unsigned)((in.ntarg + APPLY_TILE - 1) / APPLY_TILE), APPLY_TILE, 0, s.st>>>(
+                kernel, in.xyz, in.nrm, in.wts, d_sig, in.nnode, in.txyz, in.tnrm, in.ntarg, rc2, d_out);
+        else
+            k_apply<<<(unsigned)((in.ntarg + APPLY_TILE - 1) / APPLY_TILE), APPLY_TILE, 0, s.st>>>(
+                kernel, in.xyz, in.nrm, in.wts, d_sig, in.nnode, in.txyz, in.tnrm, in.tself, in.ntarg, d_out);
         CK(cudaGetLastError());
         CK(cudaEventRecord(ctx->ev[1], s.st));
-        if (val) {
+        if (mixed)
+            k_spmv_near64<<<(unsigned)((in.ntarg * 32 + 255) / 256), 256, 0, s.st>>>(
+                kernel, corr->rowptr, corr->col, val, d_sig, in.xyz, in.nrm, in.wts, in.txyz, in.tnrm, in.tself, rc2,
+                in.ntarg, d_out);
+        else if (val)
             k_spmv<<<(unsigned)((in.ntarg * 32 + 255) / 256), 256, 0, s.st>>>(corr->rowptr, corr->col, val, d_sig,
                                                                               in.ntarg, d_out);
-            CK(cudaGetLastError());
-        }
+        CK(cudaGetLastError());
         CK(cudaEventRecord(ctx->ev[2], s.st));
     }
     if (o.inputs_on_host && in.ntarg > 0)

@@ -335,6 +335,12 @@ rrq_status create_impl(rrq_ctx *ctx, rrq_batch *b, int32_t nsurf, const rrq_surf
         for (int p = 2; p <= RRQ_PMAX; p++)
             if (b->it1[p] > b->it0[p]) CK(autotune_order(b, p, st));
         b->ms_autotune = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        // later builds on this context use the measured shapes
+        for (int p = 2; p <= RRQ_PMAX; p++)
+            if (b->it1[p] > b->it0[p]) {
+                ctx->tune_tile[b->mixed][p] = b->tile[p];
+                ctx->tune_pers[b->mixed][p] = b->persistent[p];
+            }
     }
     // record the value computation as one graph (on a private stream)
     CK(cudaStreamSynchronize(st));
@@ -471,4 +477,13 @@ extern "C" void rrq_batch_destroy(rrq_batch *b) {
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     delete b;
+}
+
+extern "C" rrq_status rrq_autotune(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, uint32_t kernel_mask,
+                                   const rrq_options *opt) {
+    rrq_batch *b = nullptr;
+    const rrq_status rs = rrq_batch_create(ctx, 1, surf, targ, kernel_mask, opt, RRQ_BATCH_AUTOTUNE, &b);
+    if (rs != RRQ_OK) return rs;
+    rrq_batch_destroy(b);
+    return RRQ_OK;
 }

@@ -37,6 +37,10 @@ struct rrq_ctx {
     OrderTables *d_tab[RRQ_PMAX + 1];
     std::vector<double> tab_key[RRQ_PMAX + 1];
     double tab_rho0[RRQ_PMAX + 1];
+    // launch shapes of the per-pair stage measured by the autotuner, per [mixed][order]
+    // (tile 0 = not tuned: the order's default tile, grid-stride schedule)
+    int tune_tile[2][RRQ_PMAX + 1];
+    int tune_pers[2][RRQ_PMAX + 1];
 };
 
 // scratch allocator: stream-ordered allocations freed together

@@ -99,6 +99,8 @@ def load(build_if_needed: bool = True):
             L.rrq_batch_csr.argtypes = [C.c_void_p, C.c_int32, C.POINTER(CSR), C.c_void_p, C.c_void_p]
             L.rrq_batch_info_get.argtypes = [C.c_void_p, C.POINTER(BatchInfo)]
             L.rrq_batch_destroy.argtypes = [C.c_void_p]
+            L.rrq_autotune.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS), C.c_uint32,
+                                       C.POINTER(Options)]
             _lib = L
     return _lib
 
@@ -204,6 +206,15 @@ class Context:
         """Batch plan over several surfaces (rrq_batch_create); see Batch."""
         return Batch(self, surfs, targs, kernels, mixed, autotune, inputs_on_host)
 
+    def autotune(self, surf: Surface, targ: TargetsS, kernels=("S", "D", "SP", "DP"), mixed: bool = False):
+        """Measure the per-pair launch shapes on this problem and keep them in the context
+        (rrq_autotune)."""
+        mask = 0
+        for k in kernels:
+            mask |= KERNEL_BITS[k]
+        opt = Options(0, 0, 0.0, 0, 0.0, int(mixed))
+        _check(self.L.rrq_autotune(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt)), "rrq_autotune")
+
     def csr_free(self, csr: CSR):
         _check(self.L.rrq_csr_free(self.h, C.byref(csr)), "rrq_csr_free")
 
@@ -233,8 +244,8 @@ class Context:
         return rowptr, col, vals
 
     def apply(self, surf: Surface, targ: TargetsS, kernel: str, csr: CSR, density, out,
-              inputs_on_host: bool = False):
-        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, 0)
+              inputs_on_host: bool = False, mixed: bool = False):
+        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, int(mixed))
         _check(self.L.rrq_apply(self.h, C.byref(surf), C.byref(targ), KERNEL_BITS[kernel],
                                 C.byref(csr) if csr is not None else None, _ptr(density), _ptr(out),
                                 C.byref(opt)), "rrq_apply")

@@ -145,3 +145,20 @@ def test_batch_view_apply_and_errors(ctx, batch_data):
     s2 = ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], bad)
     with pytest.raises(R.RRQError, match="invalid argument"):
         ctx.batch([st[0][0], s2], [st[0][1], st[0][1]])
+
+
+def test_autotune_keeps_values(batch_data):
+    """rrq_autotune changes only the launch shape of later builds on the context."""
+    from paper_2411_08342_gb300 import rrq
+    c = rrq.Context(0)
+    try:
+        d, tg = batch_data[4]
+        before = gpu_build(c, d, tg)
+        surf, targ = _surf_targ(c, d, tg)
+        c.autotune(surf, targ)
+        after = gpu_build(c, d, tg)
+        assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+        for k in KINDS:
+            assert np.array_equal(before[2][k], after[2][k]), k
+    finally:
+        c.close()

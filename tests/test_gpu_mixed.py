@@ -56,3 +56,41 @@ def test_mixed_against_oracle(ctx, oracle_lib, name):
         print(name, k, f"row {e:.1e} (oracle self {er:.1e}) apply {ea:.1e} (oracle self {era:.1e})")
         assert e <= max(TOL_E, MIXED_ROW_FACTOR * er), (k, e, er)
         assert ea <= max(TOL_APPLY, ROT_FACTOR * era), (k, ea, era)
+
+
+def test_mixed_apply_direct_sum(ctx):
+    """rrq_apply with precision = 1: smooth terms of sources at least r_c from the target
+    in FP32 (hi/lo coordinates, compensated tile sums), closer ones (all in the target's
+    CSR row) in FP64 with the correction.  Stated tolerance: per target,
+    |apply_mixed - apply_fp64| <= 1e-6 x (sum_j |K(t, x_j) w_j sigma_j| + sum_j |C_tj sigma_j|),
+    for off-surface targets down to 1e-6 h and all four kernels."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    from oracle import brute
+    d, tg = W.star1280(6, 2000, seed=21)
+    sig = W.random_ylm_density(d.xyz, 8, seed=4)
+    arrs = rrq.device_inputs(d, tg)
+    surf = ctx.surface(arrs["order"], arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
+    targ = ctx.targets(arrs["txyz"], arrs["tnrm"], arrs["tself"])
+    csr = ctx.build_corrections(surf, targ)
+    rowptr, col, vals = ctx.csr_to_host(csr)
+    sdev = torch.as_tensor(sig, dtype=torch.float64, device="cuda")
+    try:
+        for k in KINDS:
+            o64 = torch.empty(tg.n, dtype=torch.float64, device="cuda")
+            o32 = torch.empty_like(o64)
+            ctx.apply(surf, targ, k, csr, sdev, o64)
+            ctx.apply(surf, targ, k, csr, sdev, o32, mixed=True)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                K = brute.kernel(k, tg.xyz[:, None], tg.nrm[:, None], d.xyz[None], d.nrm[None])
+            nnz = int(rowptr[-1])
+            ca = np.add.reduceat(np.abs(vals[k][:nnz] * sig[col[:nnz]]), rowptr[:-1])
+            scale = np.abs(K) @ np.abs(d.wts * sig) + ca
+            g64, g32 = o64.cpu().numpy(), o32.cpu().numpy()
+            err = np.max(np.abs(g32 - g64) / scale)
+            print(k, f"mixed apply rel. error {err:.1e} (plain {np.abs(g32 - g64).max() / np.abs(g64).max():.1e})")
+            assert err <= 1e-6, (k, err)
+        with pytest.raises(rrq.RRQError, match="invalid argument"):
+            ctx.apply(surf, targ, "S", None, sdev, o32, mixed=True)
+    finally:
+        ctx.csr_free(csr)
