@@ -231,6 +231,34 @@ class Context:
         _check(self.L.rrq_csr_copy(self.h, C.byref(csr), _ptr(rowptr), _ptr(col), arr, 0), "rrq_csr_copy")
         return rowptr, col[: csr.nnz], {k: v[: csr.nnz] for k, v in vals.items()}
 
+    def csr_rows_to_host(self, csr: CSR, rows, kernels=("S", "D", "SP", "DP")):
+        """Selected rows of a library CSR as a compact host CSR (rowptr, col, {kernel: val}),
+        copied row by row through CSR views (rrq_csr_copy), without copying the matrix."""
+        full_rowptr = np.empty(csr.nrows + 1, np.int64)
+        _check(self.L.rrq_csr_copy(self.h, C.byref(csr), _ptr(full_rowptr), None, (C.c_void_p * 4)(), 1),
+               "rrq_csr_copy")
+        rows = np.asarray(rows, np.int64)
+        lens = full_rowptr[rows + 1] - full_rowptr[rows]
+        rowptr = np.zeros(len(rows) + 1, np.int64)
+        np.cumsum(lens, out=rowptr[1:])
+        col = np.empty(max(int(rowptr[-1]), 1), np.int32)
+        vals = {k: np.empty(max(int(rowptr[-1]), 1), np.float64) for k in kernels}
+        for i, t in enumerate(rows):
+            v = CSR()
+            v.nrows, v.nnz, v.npairs = 1, int(lens[i]), 0
+            v.kernel_mask = csr.kernel_mask | CSR_VIEW
+            v.rowptr = csr.rowptr + 8 * int(t)
+            v.col = csr.col
+            for k in range(4):
+                v.val[k] = csr.val[k]
+            arr = (C.c_void_p * 4)()
+            for k, a in vals.items():
+                arr[KERNEL_SLOT[k]] = a.ctypes.data + 8 * int(rowptr[i])
+            _check(self.L.rrq_csr_copy(self.h, C.byref(v), None, col.ctypes.data + 4 * int(rowptr[i]), arr, 1),
+                   "rrq_csr_copy")
+        n = int(rowptr[-1])
+        return rowptr, col[:n], {k: a[:n] for k, a in vals.items()}
+
     def csr_to_host(self, csr: CSR, kernels=("S", "D", "SP", "DP"), out=None):
         """Copy a library CSR into (pinned or plain) numpy host buffers."""
         if out is None:

@@ -41,15 +41,16 @@ def rotated(d, tg, rotvec=ROT_VEC):
 def apply_error(kind, d, tg, rowptr, col, v_gpu, v_orc, sigma, plain=False):
     """max_t |((C_gpu - C_orc) sigma)_t| / (sum_j |K(t,x_j) w_j sigma_j| + sum_j |C_orc[t,j] sigma_j|);
     with plain=True the denominator is |(smooth + C_orc) sigma|_inf instead."""
+    ch = max(1, min(512, 4_000_000 // len(d.xyz)))   # targets per chunk: bounded temporaries
     with np.errstate(divide="ignore", invalid="ignore"):
         sm = np.zeros(len(rowptr) - 1)
         sa = np.zeros(len(rowptr) - 1)
-        for c0 in range(0, len(sm), 512):
-            K = brute.kernel(kind, tg.xyz[c0:c0 + 512, None], tg.nrm[c0:c0 + 512, None], d.xyz[None], d.nrm[None])
-            sn = tg.self_node[c0:c0 + 512]
+        for c0 in range(0, len(sm), ch):
+            K = brute.kernel(kind, tg.xyz[c0:c0 + ch, None], tg.nrm[c0:c0 + ch, None], d.xyz[None], d.nrm[None])
+            sn = tg.self_node[c0:c0 + ch]
             K[np.arange(len(sn))[sn >= 0], sn[sn >= 0]] = 0.0
-            sm[c0:c0 + 512] = K @ (d.wts * sigma)
-            sa[c0:c0 + 512] = np.abs(K) @ np.abs(d.wts * sigma)
+            sm[c0:c0 + ch] = K @ (d.wts * sigma)
+            sa[c0:c0 + ch] = np.abs(K) @ np.abs(d.wts * sigma)
     nz = np.diff(rowptr) > 0
     cg = np.zeros(len(sm))
     co = np.zeros(len(sm))
@@ -103,3 +104,22 @@ def gpu_build(ctx, d, tg, kernels=KINDS, on_host=False, **kw):
     torch.cuda.synchronize()
     nnz = int(rowptr[-1])
     return rowptr, col[:nnz], {k: v[:nnz] for k, v in vals.items()}, diag
+
+
+def gpu_build_sampled(ctx, d, tg, tsel, kernels=KINDS, **kw):
+    """Build the whole problem on the GPU (device inputs) and copy back only the rows
+    tsel, as a compact CSR; for problems whose matrices are too large to copy."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    arrs = rrq.device_inputs(d, tg)
+    surf = ctx.surface(arrs["order"], arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
+    targ = ctx.targets(arrs["txyz"], arrs["tnrm"], arrs["tself"])
+    csr = ctx.build_corrections(surf, targ, kernels, **kw)
+    diag = ctx.diagnostics()
+    try:
+        rowptr, col, vals = ctx.csr_rows_to_host(csr, tsel, kernels)
+    finally:
+        ctx.csr_free(csr)
+        del arrs
+        torch.cuda.synchronize()
+    return rowptr, col, vals, diag

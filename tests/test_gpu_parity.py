@@ -8,8 +8,8 @@ import numpy as np
 import pytest
 
 from paper_2411_08342_gb300 import workloads as W
-from tests.gpu_helpers import (KINDS, ROT_FACTOR, TOL_APPLY, TOL_E, apply_error, gpu_build, rotated,
-                               row_error)
+from tests.gpu_helpers import (KINDS, ROT_FACTOR, TOL_APPLY, TOL_E, apply_error, gpu_build, gpu_build_sampled,
+                               rotated, row_error)
 
 pytestmark = pytest.mark.gpu
 
@@ -25,10 +25,18 @@ def ctx():
     c.close()
 
 
-def _compare(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_host=False):
-    rowptr, col, vals, diag = gpu_build(ctx, d, tg, kernels, on_host=on_host)
+def _compare(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_host=False, sampled=False):
+    if sampled:
+        # only the selected rows come back from the device; compare them directly
+        grp, gcol, gvals, diag = gpu_build_sampled(ctx, d, tg, tsel, kernels)
+        rowptr, col, vals, tsel = grp, gcol, gvals, np.asarray(tsel)
+    else:
+        rowptr, col, vals, diag = gpu_build(ctx, d, tg, kernels, on_host=on_host)
     osf = oracle_lib.OracleSurface(d)
-    if tsel is None:
+    if sampled:
+        orp, ocol, ovals, _ = osf.csr_rows(tg, tsel, kernels=kernels)
+        sub = W.Targets(tg.xyz[tsel], tg.nrm[tsel], tg.self_node[tsel])
+    elif tsel is None:
         orp, ocol, ovals, _ = osf.csr_rows(tg, kernels=kernels)
         grp, gcol, gvals = rowptr, col, vals
         sub = tg
@@ -152,6 +160,28 @@ def test_full_size_sampled_rows(ctx, oracle_lib):
     tsel = np.sort(rng.choice(tg.n, 200, replace=False))
     errs, diag = _compare(ctx, oracle_lib, d, tg, tsel)
     assert diag["npairs"] > 200_000 * 10
+
+
+def test_full_size_torus_p8_sampled(ctx, oracle_lib):
+    """The wavy-torus workload (20,480 patches, p = 8; 737,280 on-surface nodes and
+    200,000 off-surface targets) built in full on the GPU; 60 seeded on-surface and 60
+    off-surface rows copied back and checked against the oracle."""
+    d, tg = W.wavy_torus()
+    non = d.nnode
+    rng = np.random.default_rng(12)
+    tsel = np.sort(np.concatenate([rng.choice(non, 60, replace=False), non + rng.choice(tg.n - non, 60, replace=False)]))
+    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, sampled=True)
+    assert diag["npairs"] > 10_000_000
+
+
+def test_full_size_ellipsoid_sampled(ctx, oracle_lib):
+    """The ellipsoid (2, 1, 0.5) on 81,920 patches, p = 6, all 1,720,320 on-surface nodes
+    as targets, built in full on the GPU; 100 seeded rows checked against the oracle."""
+    d, tg = W.ellipsoid81920()
+    rng = np.random.default_rng(13)
+    tsel = np.sort(rng.choice(tg.n, 100, replace=False))
+    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, sampled=True)
+    assert diag["npairs"] > 20_000_000
 
 
 def test_apply_matches_reference(ctx, oracle_lib):
