@@ -35,6 +35,21 @@ __device__ __forceinline__ void dfmac(dfa &acc, float ah, float al, float bh, fl
 
 __device__ __forceinline__ double dfval(const dfa &a) { return (double)a.h + (double)a.l; }
 
+// Item f of phase K: (pair, harmonic jk) with the j >= 2 harmonics (jk >= 3) of all pairs
+// first, then the two j = 1 harmonics of all pairs.
+template <int NJK>
+__device__ __forceinline__ void kitem(int f, int nt, int &pl, int &jk) {
+    constexpr int N2 = NJK - 3;
+    if (f < nt * N2) {
+        pl = f / N2;
+        jk = 3 + f % N2;
+    } else {
+        const int g = f - nt * N2;
+        pl = g >> 1;
+        jk = 1 + (g & 1);
+    }
+}
+
 template <int P, bool MIX, int T>
 __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned long long *tile_ctr) {
     const OrderTables *__restrict__ tab = a.tab;
@@ -60,6 +75,17 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
     __shared__ double s_uz[T];
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const bool wantDP = (mask & RRQ_DP) != 0;
+    // kernel groups of the row phase that this build needs
+    __shared__ int s_grp[3];
+    int ngrp = 0;
+    {
+        int g[3], n = 0;
+        if (mask & (RRQ_D | RRQ_DP)) g[n++] = 0;
+        if (mask & RRQ_SP) g[n++] = 1;
+        if (mask & RRQ_S) g[n++] = 2;
+        if (tid < n) s_grp[tid] = g[tid];
+        ngrp = n;
+    }
     if (tid < 5) bc[tid] = 0;
     const double inv4pi = 0.07957747154594767, sq2 = 1.4142135623730951;
     constexpr double FACT[2 * RRQ_PMAX + 2] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0, 5040.0, 40320.0, 362880.0,
@@ -401,10 +427,13 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
         }
         __syncthreads();
-        // K: line integrals, one thread per (pair, (j, k >= 0)), j >= 1
+        // K: line integrals, one thread per (pair, (j, k >= 0)), j >= 1; the items with j >= 2
+        // (V, Q, dQ) come first and the cheap j = 1 items (V only) last, so that warps do not
+        // mix the two
         if (MIX) {
             for (int f = tid; f < nt * (NJK - 1); f += nth) {
-                const int pl = f / (NJK - 1), jk = 1 + f % (NJK - 1);
+                int pl, jk;
+                kitem<NJK>(f, nt, pl, jk);
                 double *sw = SW(pl);
                 const size_t ps = (size_t)s_item[pl].P;
                 const float *wf = reinterpret_cast<const float *>(sw + Z::WV);
@@ -469,7 +498,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
         } else
         for (int f = tid; f < nt * (NJK - 1); f += nth) {
-            const int pl = f / (NJK - 1), jk = 1 + f % (NJK - 1);
+            int pl, jk;
+            kitem<NJK>(f, nt, pl, jk);
             double *sw = SW(pl);
             const size_t ps = (size_t)s_item[pl].P;
             const double *wv = sw + Z::WV, *nut = sw + Z::NUT;
@@ -528,9 +558,23 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
         }
         __syncthreads();
+        // L0: nu' derivative of the target harmonics, dS^{(n,q)} = grad S^{(n,q)}(y') . nu', per
+        // (pair, (n, q >= 0)), into the singularity-swap scratch (dead after phase G2)
+        if (wantDP) {
+            for (int f = tid; f < nt * NJK; f += nth) {
+                const int pl = f / NJK, jk = f % NJK;
+                double *sw = SW(pl);
+                const double *nut = sw + Z::NUT;
+                const cd *gg = reinterpret_cast<const cd *>(sw + Z::GST) + 3 * jk;
+                reinterpret_cast<cd *>(sw + Z::UP)[jk] =
+                    mkc(fma(gg[0].x, nut[0], fma(gg[1].x, nut[1], gg[2].x * nut[2])),
+                        fma(gg[0].y, nut[0], fma(gg[1].y, nut[1], gg[2].y * nut[2])));
+            }
+            __syncthreads();
+        }
         // L: translations and I[gamma], one thread per (pair, (l, m)); items ordered with
         // the largest l first and the pair index fastest, so that the lanes of a warp
-        // run loops of similar length
+        // run loops of similar length.  The factors C_{j,l}, D_{j,l} multiply each j's sum.
         for (int f = tid; f < nt * NP; f += nth) {
             const int pl = f % nt, lm = NP - 1 - f / nt;
             double *sw = SW(pl);
@@ -538,44 +582,45 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const cd *St = reinterpret_cast<const cd *>(sw + Z::ST), *gSt = reinterpret_cast<const cd *>(sw + Z::GST);
             const cd *HSt = reinterpret_cast<const cd *>(sw + Z::HST), *Qs = reinterpret_cast<const cd *>(sw + Z::Q);
             const cd *dQs = reinterpret_cast<const cd *>(sw + Z::DQQ), *Vs = reinterpret_cast<const cd *>(sw + Z::V);
+            const cd *dSt = reinterpret_cast<const cd *>(sw + Z::UP);
             int l = 1;
             while ((l + 1) * l / 2 <= lm) l++;
             const int m = lm - l * (l - 1) / 2 + 1;
             double Ib0 = 0, Ib1 = 0, Ib2 = 0, Ib3 = 0, Ip = 0, dI0 = 0, dI1 = 0, dI2 = 0, dI3 = 0;
             for (int j = 1; j <= l; j++) {
                 const double Dj = FACT[j - 1] * FACT[l - j] / FACT[l];
-                const double Cj = j >= 2 ? FACT[j - 2] * FACT[l - j] / FACT[l - 1] : 0.0;
                 const int kmin = max(-j, m - (l - j)), kmax = min(j, m + (l - j));
+                double ip = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0, e0s = 0, e1s = 0, e2s = 0, e3s = 0;
                 for (int k = kmin; k <= kmax; k++) {
                     const int ak = k < 0 ? -k : k;
                     const int jkx = jk_index(j, ak);
                     const cd Sv = tget(St, l - j, m - k);
                     const cd v = kflip(Vs[jkx], k);
-                    Ip = fma(Dj, fma(v.x, Sv.y, v.y * Sv.x), Ip);
+                    ip = fma(v.x, Sv.y, fma(v.y, Sv.x, ip));
                     if (j >= 2) {
                         const cd q0 = kflip(Qs[4 * jkx], k), q1 = kflip(Qs[4 * jkx + 1], k);
                         const cd q2 = kflip(Qs[4 * jkx + 2], k), q3 = kflip(Qs[4 * jkx + 3], k);
-                        const cd cs = cscale(Sv, Cj);
-                        Ib0 = fma(q0.x, cs.y, fma(q0.y, cs.x, Ib0));
-                        Ib1 = fma(q1.x, cs.y, fma(q1.y, cs.x, Ib1));
-                        Ib2 = fma(q2.x, cs.y, fma(q2.y, cs.x, Ib2));
-                        Ib3 = fma(q3.x, cs.y, fma(q3.y, cs.x, Ib3));
+                        b0 = fma(q0.x, Sv.y, fma(q0.y, Sv.x, b0));
+                        b1 = fma(q1.x, Sv.y, fma(q1.y, Sv.x, b1));
+                        b2 = fma(q2.x, Sv.y, fma(q2.y, Sv.x, b2));
+                        b3 = fma(q3.x, Sv.y, fma(q3.y, Sv.x, b3));
                         if (wantDP) {
-                            const int n = l - j, qq = m - k, aq = qq < 0 ? -qq : qq;
-                            cd dS = mkc(0, 0);
-                            if (aq <= n) {
-                                const cd *gg = gSt + 3 * jk_index(n, aq);
-                                dS = cadd(cadd(cscale(gg[0], nut[0]), cscale(gg[1], nut[1])), cscale(gg[2], nut[2]));
-                                dS = kflip(dS, qq);
-                            }
-                            const cd c2 = cscale(dS, Cj);
+                            const cd dS = tget(dSt, l - j, m - k);
                             const cd e0 = kflip(dQs[4 * jkx], k), e1 = kflip(dQs[4 * jkx + 1], k);
                             const cd e2 = kflip(dQs[4 * jkx + 2], k), e3 = kflip(dQs[4 * jkx + 3], k);
-                            dI0 = fma(e0.x, cs.y, fma(e0.y, cs.x, fma(q0.x, c2.y, fma(q0.y, c2.x, dI0))));
-                            dI1 = fma(e1.x, cs.y, fma(e1.y, cs.x, fma(q1.x, c2.y, fma(q1.y, c2.x, dI1))));
-                            dI2 = fma(e2.x, cs.y, fma(e2.y, cs.x, fma(q2.x, c2.y, fma(q2.y, c2.x, dI2))));
-                            dI3 = fma(e3.x, cs.y, fma(e3.y, cs.x, fma(q3.x, c2.y, fma(q3.y, c2.x, dI3))));
+                            e0s = fma(e0.x, Sv.y, fma(e0.y, Sv.x, fma(q0.x, dS.y, fma(q0.y, dS.x, e0s))));
+                            e1s = fma(e1.x, Sv.y, fma(e1.y, Sv.x, fma(q1.x, dS.y, fma(q1.y, dS.x, e1s))));
+                            e2s = fma(e2.x, Sv.y, fma(e2.y, Sv.x, fma(q2.x, dS.y, fma(q2.y, dS.x, e2s))));
+                            e3s = fma(e3.x, Sv.y, fma(e3.y, Sv.x, fma(q3.x, dS.y, fma(q3.y, dS.x, e3s))));
                         }
+                    }
+                }
+                Ip = fma(Dj, ip, Ip);
+                if (j >= 2) {
+                    const double Cj = FACT[j - 2] * FACT[l - j] / FACT[l - 1];
+                    Ib0 = fma(Cj, b0, Ib0); Ib1 = fma(Cj, b1, Ib1); Ib2 = fma(Cj, b2, Ib2); Ib3 = fma(Cj, b3, Ib3);
+                    if (wantDP) {
+                        dI0 = fma(Cj, e0s, dI0); dI1 = fma(Cj, e1s, dI1); dI2 = fma(Cj, e2s, dI2); dI3 = fma(Cj, e3s, dI3);
                     }
                 }
             }
@@ -587,10 +632,20 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const cd G3 = cadd(cscale(g[2], W0), csub(cscale(g[1], W1), cscale(g[0], W2)));
             const double fct = sq2 * inv4pi;
             double *Bs = sw + Z::B, *Bds = sw + Z::BD;
-            Bs[4 * lm] = fct * (Ib0 + G0.y);
-            Bs[4 * lm + 1] = fct * (Ib1 + G1.y);
-            Bs[4 * lm + 2] = fct * (Ib2 + G2.y);
-            Bs[4 * lm + 3] = fct * (Ib3 + G3.y);
+            const double B0 = fct * (Ib0 + G0.y), B1 = fct * (Ib1 + G1.y), B2 = fct * (Ib2 + G2.y), B3 = fct * (Ib3 + G3.y);
+            Bs[4 * lm] = B0;
+            Bs[4 * lm + 1] = B1;
+            Bs[4 * lm + 2] = B2;
+            Bs[4 * lm + 3] = B3;
+            {
+                // (0, nu') B, whose product with the S' fit gives the S' row (eq. sprime1formrep)
+                const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
+                double *Bp = sw + Z::DQ + 4 * lm;
+                Bp[0] = n0 * B1 + n1 * B2 + n2 * B3;
+                Bp[1] = B0 * n0 + (n1 * B3 - n2 * B2);
+                Bp[2] = B0 * n1 + (n2 * B1 - n0 * B3);
+                Bp[3] = B0 * n2 + (n0 * B2 - n1 * B1);
+            }
             sw[Z::PSI + lm] = fct * (Ip + St[jk_index(l, m)].y * Om[0]);
             if (wantDP) {
                 const double X0 = Om[4], X1 = Om[5], X2 = Om[6], X3 = Om[7];
@@ -614,44 +669,45 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
         }
         __syncthreads();
-        // M: rows, one thread per (pair, node)
-        for (int f = tid; f < nt * NP; f += nth) {
-            const int pl = f / NP, i = f % NP;
+        // M: rows through the fit matrices (Step 8), jump and smooth subtraction; one thread per
+        // (kernel group, pair, node), groups {D, D'} (X_D), {S'} (X_S'), {S} (X_S2, X_S1)
+        for (int f = tid; f < nt * NP * ngrp; f += nth) {
+            const int grp = s_grp[f / (nt * NP)], rem = f % (nt * NP), pl = rem / NP, i = rem % NP;
             const double *sw = SW(pl);
             const PairItem im = s_item[pl];
             const size_t ps = (size_t)im.P;
-            const double *XD = pd.XD + ps * pd_X(), *XSp = pd.XSp + ps * pd_X(), *XS2 = pd.XS2 + ps * pd_X();
-            const double *XS1 = pd.XS1 + ps * pd_XS1();
-            const double *Bs = sw + Z::B, *Bds = sw + Z::BD, *Psis = sw + Z::PSI, *nut = sw + Z::NUT, *fr = sw + Z::FR;
-            const double sc = fr[12], Lsc = 1.0 / sc;
-            const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
-            double rS = 0, rD = 0, rSp = 0, rDp = 0;
-            for (int lm = 0; lm < NP; lm++) {
-                const double B0 = Bs[4 * lm], B1 = Bs[4 * lm + 1], B2 = Bs[4 * lm + 2], B3 = Bs[4 * lm + 3];
-                const double x0 = XD[(0 * NP + lm) * NP + i], x1 = XD[(1 * NP + lm) * NP + i];
-                const double x2 = XD[(2 * NP + lm) * NP + i], x3 = XD[(3 * NP + lm) * NP + i];
-                rD -= B0 * x0 - B1 * x1 - B2 * x2 - B3 * x3;
-                if (wantDP)
-                    rDp -= Bds[4 * lm] * x0 - Bds[4 * lm + 1] * x1 - Bds[4 * lm + 2] * x2 - Bds[4 * lm + 3] * x3;
-                if (mask & RRQ_SP) {
-                    const double w0 = XSp[(0 * NP + lm) * NP + i], w1 = XSp[(1 * NP + lm) * NP + i];
-                    const double w2 = XSp[(2 * NP + lm) * NP + i], w3 = XSp[(3 * NP + lm) * NP + i];
-                    const double nB = n0 * B1 + n1 * B2 + n2 * B3;
-                    const double c0 = n1 * B3 - n2 * B2, c1 = n2 * B1 - n0 * B3, c2 = n0 * B2 - n1 * B1;
-                    rSp += nB * w0 + (B0 * n0 + c0) * w1 + (B0 * n1 + c1) * w2 + (B0 * n2 + c2) * w3;
+            const double *fr = sw + Z::FR;
+            const double sc = fr[12];
+            double r0 = 0, r1 = 0;  // group 0: D, D'; group 1: S'; group 2: S
+            if (grp == 0) {
+                const double *X = pd.XD + ps * pd_X(), *Bs = sw + Z::B, *Bds = sw + Z::BD;
+                for (int lm = 0; lm < NP; lm++) {
+                    const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
+                    const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
+                    r0 -= Bs[4 * lm] * x0 - Bs[4 * lm + 1] * x1 - Bs[4 * lm + 2] * x2 - Bs[4 * lm + 3] * x3;
+                    if (wantDP)
+                        r1 -= Bds[4 * lm] * x0 - Bds[4 * lm + 1] * x1 - Bds[4 * lm + 2] * x2 - Bds[4 * lm + 3] * x3;
                 }
-                if (mask & RRQ_S) {
-                    const double g0 = XS2[(0 * NP + lm) * NP + i], g1 = XS2[(1 * NP + lm) * NP + i];
-                    const double g2 = XS2[(2 * NP + lm) * NP + i], g3 = XS2[(3 * NP + lm) * NP + i];
-                    rS += Psis[lm] * XS1[lm * NP + i] - (B0 * g0 - B1 * g1 - B2 * g2 - B3 * g3);
-                }
+                r1 *= sc;
+            } else if (grp == 1) {
+                const double *X = pd.XSp + ps * pd_X(), *Bp = sw + Z::DQ;
+                for (int lm = 0; lm < NP; lm++)
+                    r0 += Bp[4 * lm] * X[(0 * NP + lm) * NP + i] + Bp[4 * lm + 1] * X[(1 * NP + lm) * NP + i] +
+                          Bp[4 * lm + 2] * X[(2 * NP + lm) * NP + i] + Bp[4 * lm + 3] * X[(3 * NP + lm) * NP + i];
+            } else {
+                const double *X = pd.XS2 + ps * pd_X(), *X1 = pd.XS1 + ps * pd_XS1(), *Bs = sw + Z::B;
+                const double *Psis = sw + Z::PSI;
+                for (int lm = 0; lm < NP; lm++)
+                    r0 += Psis[lm] * X1[lm * NP + i] -
+                          (Bs[4 * lm] * X[(0 * NP + lm) * NP + i] - Bs[4 * lm + 1] * X[(1 * NP + lm) * NP + i] -
+                           Bs[4 * lm + 2] * X[(2 * NP + lm) * NP + i] - Bs[4 * lm + 3] * X[(3 * NP + lm) * NP + i]);
+                r0 *= 1.0 / sc;
             }
-            rS *= Lsc;
-            rDp *= sc;
             const int64_t o = node_off[im.P];
+            const int64_t dst = im.off + i;
             if (i == s_self[pl]) {
-                rD -= 0.5;
-                rSp += 0.5;
+                if (grp == 0) r0 -= 0.5;
+                if (grp == 1) r0 += 0.5;
             } else {
                 const double *xs = xyz + 3 * (o + i), *ns = nrm + 3 * (o + i);
                 const double d0 = sw[Z::XT] - xs[0], d1 = sw[Z::XT + 1] - xs[1], d2 = sw[Z::XT + 2] - xs[2];
@@ -660,17 +716,24 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const double wk = wts[o + i] * inv4pi;
                 const double dns = d0 * ns[0] + d1 * ns[1] + d2 * ns[2];
                 const double dnt = d0 * gn0 + d1 * gn1 + d2 * gn2;
-                rS -= wk / r;
-                rD -= wk * dns / r3;
-                rSp += wk * dnt / r3;
-                rDp -= wk * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) / r3 - 3.0 * dns * dnt / (r3 * r2));
+                if (grp == 0) {
+                    r0 -= wk * dns / r3;
+                    r1 -= wk * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) / r3 - 3.0 * dns * dnt / (r3 * r2));
+                } else if (grp == 1) {
+                    r0 += wk * dnt / r3;
+                } else {
+                    r0 -= wk / r;
+                }
             }
-            const int64_t dst = im.off + i;
-            col[dst] = (int32_t)(col_off[im.P] + i);
-            if ((mask & RRQ_S) && vS) vS[dst] = rS;
-            if ((mask & RRQ_D) && vD) vD[dst] = rD;
-            if ((mask & RRQ_SP) && vSp) vSp[dst] = rSp;
-            if ((mask & RRQ_DP) && vDp) vDp[dst] = rDp;
+            if (grp == s_grp[0]) col[dst] = (int32_t)(col_off[im.P] + i);
+            if (grp == 0) {
+                if ((mask & RRQ_D) && vD) vD[dst] = r0;
+                if ((mask & RRQ_DP) && vDp) vDp[dst] = r1;
+            } else if (grp == 1) {
+                if (vSp) vSp[dst] = r0;
+            } else if (vS) {
+                vS[dst] = r0;
+            }
         }
     }
 #undef SW
