@@ -271,7 +271,8 @@ def bench_gpu(args):
                   "stage_ms": {"precompute": mdiag["ms_precompute"], "near_and_items": mdiag["ms_near"],
                                "pairs": mdiag["ms_pairs"]},
                   "speedup_vs_fp64": ms_step / ms_mixed,
-                  "precision": "Step-6 line integrals in double-float FP32 (about 48 bits), rest FP64",
+                  "precision": "line integrals, translations and fit contraction in double-float FP32 "
+                               "(about 48 bits); roots, recurrences, Omega_0, harmonics, smooth rule FP64",
                   "parity": "apply-level error as FP64; rows within 32x the oracle's own rounding sensitivity "
                             "(tests/test_gpu_mixed.py)"},
     }

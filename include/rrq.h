@@ -94,11 +94,14 @@ typedef struct {
     int32_t newton_max;      /* Newton iterations for t0; 0 = 30 */
     double eta;              /* near factor; 0 = 1 */
     int32_t precision;       /* 0: FP64 throughout (default).  1: mixed -- the line
-                                integrals of Step 6 (sums over the 3 ptilde edge nodes) are
-                                accumulated in double-float arithmetic (pairs of FP32 numbers,
-                                exact FMA products, compensated sums: about 48 bits) on the
-                                FP32 pipes; roots, SSQ recurrences, Omega_0, translations, fit
-                                contraction and smooth subtraction stay FP64 */
+                                integrals of Step 6 (sums over the 3 ptilde edge nodes), the
+                                translation sums of Step 7 and the fit contraction of Step 8
+                                are accumulated in double-float arithmetic (pairs of FP32
+                                numbers, exact FMA products, compensated sums: about 48 bits)
+                                on the FP32 pipes; roots, singularity-swap recurrences and
+                                weights, Omega_0, target harmonics and the smooth subtraction
+                                stay FP64.  In rrq_apply: the smooth sum beyond r_c in FP32
+                                (see rrq_apply) */
 } rrq_options;
 
 /* CSR correction matrix in device memory owned by the library (rrq_csr_free). */

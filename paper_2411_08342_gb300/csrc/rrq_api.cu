@@ -231,6 +231,12 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     if (o.precision != 0 && o.precision != 1) return RRQ_ERR_ARG;
     pd.eg2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
     pd.eh2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
+    if (mixed) {
+        pd.XD2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
+        pd.XSp2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
+        pd.XS22 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
+        pd.XS12 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_XS1());
+    }
     pd.XD = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
     pd.XSp = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
     pd.XS2 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());

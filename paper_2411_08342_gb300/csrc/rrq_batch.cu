@@ -237,6 +237,13 @@ rrq_status create_impl(rrq_ctx *ctx, rrq_batch *b, int32_t nsurf, const rrq_surf
     pd.eh = (cd *)b->alloc(sizeof(cd) * NP * pd_eg());
     pd.eg2 = b->mixed ? (float4 *)b->alloc(sizeof(float4) * NP * pd_eg()) : nullptr;
     pd.eh2 = b->mixed ? (float4 *)b->alloc(sizeof(float4) * NP * pd_eg()) : nullptr;
+    if (b->mixed) {
+        pd.XD2 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X());
+        pd.XSp2 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X());
+        pd.XS22 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X());
+        pd.XS12 = (float2 *)b->alloc(sizeof(float2) * NP * pd_XS1());
+        if (!pd.XD2 || !pd.XSp2 || !pd.XS22 || !pd.XS12) return RRQ_ERR_OOM;
+    }
     pd.XD = (double *)b->alloc(sizeof(double) * NP * pd_X());
     pd.XSp = (double *)b->alloc(sizeof(double) * NP * pd_X());
     pd.XS2 = (double *)b->alloc(sizeof(double) * NP * pd_X());

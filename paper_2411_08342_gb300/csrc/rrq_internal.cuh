@@ -84,6 +84,7 @@ struct PatchData {
     double *XSp;     // [P][4*NPMAX][NPMAX] quaternion fit of (0, sigma nu)
     double *XS2;     // [P][4*NPMAX][NPMAX] quaternion fit of the intermediate density
     double *XS1;     // [P][NPMAX][NPMAX]   scalar fit A_S^{-1}
+    float2 *XD2, *XSp2, *XS22, *XS12;  // the four fit matrices as (hi, lo) float pairs, or NULL
     int *status;     // [P] 0 ok, nonzero = singular fit / degenerate patch
     double *xm;      // [P][NPMAX*3] monomial coefficients [ab][a] of the local node interpolant
     EdgeRoot *roots;  // [pair item][3 edges]: (Re t0, Im t0, converged, singularity swap)

@@ -32,7 +32,9 @@ struct PairSm {
     static constexpr int NP = P * (P + 1) / 2, PT = 2 * P, NJK = (P + 1) * (P + 2) / 2, NS = 3 * PT, NUP = 2 * PT;
     static constexpr int YT = 0, NUT = 3, XT = 6, NT = 9, FR = 12;   // FR: 16
     static constexpr int EA = 28;                                     // 9P
-    static constexpr int DQ = EA + 9 * P;                             // NS*3
+    // every region from here on starts at an even double offset and TOTAL is even, so that
+    // the (hi, lo) float4 views of the mixed path are 16-byte aligned
+    static constexpr int DQ = (EA + 9 * P + 1) & ~1;                  // NS*3
     static constexpr int TAU = DQ + 3 * NS;                           // NS*3
     static constexpr int RINV = TAU + 3 * NS;                         // NS
     static constexpr int OM1 = RINV + NS;                             // NS
@@ -54,7 +56,7 @@ struct PairSm {
     static constexpr int PSI = BD + 4 * NP;                           // NP
     static constexpr int WV = PSI + NP;                               // NS*12 premultiplied sample vectors
     static constexpr int EM = WV + 12 * NS;                           // 3*P*3 monomial edge coefficients
-    static constexpr int TOTAL = EM + 9 * P + 2;
+    static constexpr int TOTAL = (EM + 9 * P + 2 + 1) & ~1;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

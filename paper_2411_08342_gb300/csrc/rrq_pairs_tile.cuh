@@ -35,6 +35,48 @@ __device__ __forceinline__ void dfmac(dfa &acc, float ah, float al, float bh, fl
 
 __device__ __forceinline__ double dfval(const dfa &a) { return (double)a.h + (double)a.l; }
 
+// (hi, lo) with |lo| <= ulp(hi) / 2 (fast two-sum)
+__device__ __forceinline__ dfa dfnorm(const dfa &a) {
+    const float s = a.h + a.l;
+    return dfa{s, a.l - (s - a.h)};
+}
+
+// acc += Im(a b) for complex numbers stored as (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ void dfim(dfa &acc, const float4 a, const float4 b) {
+    dfmac(acc, a.x, a.y, b.z, b.w);
+    dfmac(acc, a.z, a.w, b.x, b.y);
+}
+
+// complex (re, im) double-float pair of two accumulators
+__device__ __forceinline__ float4 dfc(const dfa &re, const dfa &im) {
+    const dfa r = dfnorm(re), i = dfnorm(im);
+    return make_float4(r.h, r.l, i.h, i.l);
+}
+
+// conjugation rules of tget / kflip for double-float complex tables
+__device__ __forceinline__ float4 kflip4(float4 v, int k) {
+    if (k >= 0) return v;
+    v.z = -v.z;
+    v.w = -v.w;
+    if ((-k) & 1) { v.x = -v.x; v.y = -v.y; v.z = -v.z; v.w = -v.w; }
+    return v;
+}
+__device__ __forceinline__ float4 tget4(const float4 *S, int n, int q) {
+    if (n < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const int aq = q < 0 ? -q : q;
+    if (aq > n) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return kflip4(S[jk_index(n, aq)], q);
+}
+
+__device__ __forceinline__ float4 split4c(cd v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+__device__ __forceinline__ float2 split2d(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
 // Item f of phase K: (pair, harmonic jk) with the j >= 2 harmonics (jk >= 3) of all pairs
 // first, then the two j = 1 harmonics of all pairs.
 template <int NJK>
@@ -67,7 +109,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
     BuildCounters *cnt = a.cnt;
     using Z = PairSm<P>;
     constexpr int NP = Z::NP, PT = Z::PT, NJK = Z::NJK, NS = Z::NS, NUP = Z::NUP;
-    extern __shared__ double smraw[];
+    extern __shared__ __align__(16) double smraw[];
     __shared__ unsigned int bc[5];
     __shared__ PairItem s_item[T];
     __shared__ int64_t s_base;
@@ -127,6 +169,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 }
                 sw[Z::YT + b] = fr[12] * sy;
                 sw[Z::NUT + b] = sn;
+                if (MIX) reinterpret_cast<float2 *>(sw + Z::FR + 13)[b] = split2d(sn);
             } else {
                 const int64_t o = node_off[im.P];
                 int si = -1;
@@ -481,19 +524,30 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                         }
                     }
                 }
-                cd *Vs = reinterpret_cast<cd *>(sw + Z::V), *Qs = reinterpret_cast<cd *>(sw + Z::Q);
-                cd *dQs = reinterpret_cast<cd *>(sw + Z::DQQ);
-                Vs[jk] = mkc(dfval(Vr), dfval(Vi));
-                Qs[4 * jk] = mkc(dfval(Q0r), dfval(Q0i)); Qs[4 * jk + 1] = mkc(dfval(Q1r), dfval(Q1i));
-                Qs[4 * jk + 2] = mkc(dfval(Q2r), dfval(Q2i)); Qs[4 * jk + 3] = mkc(dfval(Q3r), dfval(Q3i));
+                // results stay double-float: (re.hi, re.lo, im.hi, im.lo) per complex value
+                float4 *Vf = reinterpret_cast<float4 *>(sw + Z::V), *Qf = reinterpret_cast<float4 *>(sw + Z::Q);
+                float4 *dQf = reinterpret_cast<float4 *>(sw + Z::DQQ);
+                Vf[jk] = dfc(Vr, Vi);
+                Qf[4 * jk] = dfc(Q0r, Q0i); Qf[4 * jk + 1] = dfc(Q1r, Q1i);
+                Qf[4 * jk + 2] = dfc(Q2r, Q2i); Qf[4 * jk + 3] = dfc(Q3r, Q3i);
                 if (wantDP) {
-                    const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
-                    const double d0r = dfval(D0r), d0i = dfval(D0i), d1r = dfval(D1r), d1i = dfval(D1i);
-                    const double d2r = dfval(D2r), d2i = dfval(D2i);
-                    dQs[4 * jk] = mkc(-(n0 * d0r + n1 * d1r + n2 * d2r) - dfval(E0r), -(n0 * d0i + n1 * d1i + n2 * d2i) - dfval(E0i));
-                    dQs[4 * jk + 1] = mkc((n1 * d2r - n2 * d1r) - dfval(E1r), (n1 * d2i - n2 * d1i) - dfval(E1i));
-                    dQs[4 * jk + 2] = mkc((n2 * d0r - n0 * d2r) - dfval(E2r), (n2 * d0i - n0 * d2i) - dfval(E2i));
-                    dQs[4 * jk + 3] = mkc((n0 * d1r - n1 * d0r) - dfval(E3r), (n0 * d1i - n1 * d0i) - dfval(E3i));
+                    // dQ = (0, nu')(0, sum w1 h) - sum (0, w3 (nu'.d) d)(0, h), components as in FP64
+                    const float2 *nf = reinterpret_cast<const float2 *>(sw + Z::FR + 13);
+                    const float2 n0 = nf[0], n1 = nf[1], n2 = nf[2];
+                    dfa a0r = {-E0r.h, -E0r.l}, a0i = {-E0i.h, -E0i.l};
+                    dfmac(a0r, -n0.x, -n0.y, D0r.h, D0r.l); dfmac(a0r, -n1.x, -n1.y, D1r.h, D1r.l); dfmac(a0r, -n2.x, -n2.y, D2r.h, D2r.l);
+                    dfmac(a0i, -n0.x, -n0.y, D0i.h, D0i.l); dfmac(a0i, -n1.x, -n1.y, D1i.h, D1i.l); dfmac(a0i, -n2.x, -n2.y, D2i.h, D2i.l);
+                    dfa a1r = {-E1r.h, -E1r.l}, a1i = {-E1i.h, -E1i.l};
+                    dfmac(a1r, n1.x, n1.y, D2r.h, D2r.l); dfmac(a1r, -n2.x, -n2.y, D1r.h, D1r.l);
+                    dfmac(a1i, n1.x, n1.y, D2i.h, D2i.l); dfmac(a1i, -n2.x, -n2.y, D1i.h, D1i.l);
+                    dfa a2r = {-E2r.h, -E2r.l}, a2i = {-E2i.h, -E2i.l};
+                    dfmac(a2r, n2.x, n2.y, D0r.h, D0r.l); dfmac(a2r, -n0.x, -n0.y, D2r.h, D2r.l);
+                    dfmac(a2i, n2.x, n2.y, D0i.h, D0i.l); dfmac(a2i, -n0.x, -n0.y, D2i.h, D2i.l);
+                    dfa a3r = {-E3r.h, -E3r.l}, a3i = {-E3i.h, -E3i.l};
+                    dfmac(a3r, n0.x, n0.y, D1r.h, D1r.l); dfmac(a3r, -n1.x, -n1.y, D0r.h, D0r.l);
+                    dfmac(a3i, n0.x, n0.y, D1i.h, D1i.l); dfmac(a3i, -n1.x, -n1.y, D0i.h, D0i.l);
+                    dQf[4 * jk] = dfc(a0r, a0i); dQf[4 * jk + 1] = dfc(a1r, a1i);
+                    dQf[4 * jk + 2] = dfc(a2r, a2i); dQf[4 * jk + 3] = dfc(a3r, a3i);
                 }
             }
         } else
@@ -560,15 +614,21 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
         __syncthreads();
         // L0: nu' derivative of the target harmonics, dS^{(n,q)} = grad S^{(n,q)}(y') . nu', per
         // (pair, (n, q >= 0)), into the singularity-swap scratch (dead after phase G2)
-        if (wantDP) {
+        // (mixed: the target harmonics as double-float pairs too, into the tangent scratch)
+        if (wantDP || MIX) {
             for (int f = tid; f < nt * NJK; f += nth) {
                 const int pl = f / NJK, jk = f % NJK;
                 double *sw = SW(pl);
                 const double *nut = sw + Z::NUT;
                 const cd *gg = reinterpret_cast<const cd *>(sw + Z::GST) + 3 * jk;
-                reinterpret_cast<cd *>(sw + Z::UP)[jk] =
-                    mkc(fma(gg[0].x, nut[0], fma(gg[1].x, nut[1], gg[2].x * nut[2])),
-                        fma(gg[0].y, nut[0], fma(gg[1].y, nut[1], gg[2].y * nut[2])));
+                const cd dS = mkc(fma(gg[0].x, nut[0], fma(gg[1].x, nut[1], gg[2].x * nut[2])),
+                                  fma(gg[0].y, nut[0], fma(gg[1].y, nut[1], gg[2].y * nut[2])));
+                if (MIX) {
+                    reinterpret_cast<float4 *>(sw + Z::UP)[jk] = split4c(dS);
+                    reinterpret_cast<float4 *>(sw + Z::TAU)[jk] = split4c(reinterpret_cast<const cd *>(sw + Z::ST)[jk]);
+                } else {
+                    reinterpret_cast<cd *>(sw + Z::UP)[jk] = dS;
+                }
             }
             __syncthreads();
         }
@@ -587,6 +647,47 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             while ((l + 1) * l / 2 <= lm) l++;
             const int m = lm - l * (l - 1) / 2 + 1;
             double Ib0 = 0, Ib1 = 0, Ib2 = 0, Ib3 = 0, Ip = 0, dI0 = 0, dI1 = 0, dI2 = 0, dI3 = 0;
+            if (MIX) {
+                // the same sums in double-float on the FP32 pipes; each j's sums in FP64 after
+                const float4 *Stf = reinterpret_cast<const float4 *>(sw + Z::TAU);
+                const float4 *dStf = reinterpret_cast<const float4 *>(sw + Z::UP);
+                const float4 *Qf = reinterpret_cast<const float4 *>(sw + Z::Q);
+                const float4 *dQf = reinterpret_cast<const float4 *>(sw + Z::DQQ);
+                const float4 *Vf = reinterpret_cast<const float4 *>(sw + Z::V);
+                for (int j = 1; j <= l; j++) {
+                    const int kmin = max(-j, m - (l - j)), kmax = min(j, m + (l - j));
+                    dfa ip = {0, 0}, b0 = {0, 0}, b1 = {0, 0}, b2 = {0, 0}, b3 = {0, 0};
+                    dfa e0s = {0, 0}, e1s = {0, 0}, e2s = {0, 0}, e3s = {0, 0};
+                    for (int k = kmin; k <= kmax; k++) {
+                        const int ak = k < 0 ? -k : k;
+                        const int jkx = jk_index(j, ak);
+                        const float4 Sv = tget4(Stf, l - j, m - k);
+                        dfim(ip, kflip4(Vf[jkx], k), Sv);
+                        if (j >= 2) {
+                            const float4 q0 = kflip4(Qf[4 * jkx], k), q1 = kflip4(Qf[4 * jkx + 1], k);
+                            const float4 q2 = kflip4(Qf[4 * jkx + 2], k), q3 = kflip4(Qf[4 * jkx + 3], k);
+                            dfim(b0, q0, Sv); dfim(b1, q1, Sv); dfim(b2, q2, Sv); dfim(b3, q3, Sv);
+                            if (wantDP) {
+                                const float4 dS = tget4(dStf, l - j, m - k);
+                                dfim(e0s, kflip4(dQf[4 * jkx], k), Sv); dfim(e0s, q0, dS);
+                                dfim(e1s, kflip4(dQf[4 * jkx + 1], k), Sv); dfim(e1s, q1, dS);
+                                dfim(e2s, kflip4(dQf[4 * jkx + 2], k), Sv); dfim(e2s, q2, dS);
+                                dfim(e3s, kflip4(dQf[4 * jkx + 3], k), Sv); dfim(e3s, q3, dS);
+                            }
+                        }
+                    }
+                    Ip = fma(FACT[j - 1] * FACT[l - j] / FACT[l], dfval(ip), Ip);
+                    if (j >= 2) {
+                        const double Cj = FACT[j - 2] * FACT[l - j] / FACT[l - 1];
+                        Ib0 = fma(Cj, dfval(b0), Ib0); Ib1 = fma(Cj, dfval(b1), Ib1);
+                        Ib2 = fma(Cj, dfval(b2), Ib2); Ib3 = fma(Cj, dfval(b3), Ib3);
+                        if (wantDP) {
+                            dI0 = fma(Cj, dfval(e0s), dI0); dI1 = fma(Cj, dfval(e1s), dI1);
+                            dI2 = fma(Cj, dfval(e2s), dI2); dI3 = fma(Cj, dfval(e3s), dI3);
+                        }
+                    }
+                }
+            } else
             for (int j = 1; j <= l; j++) {
                 const double Dj = FACT[j - 1] * FACT[l - j] / FACT[l];
                 const int kmin = max(-j, m - (l - j)), kmax = min(j, m + (l - j));
@@ -633,20 +734,23 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const double fct = sq2 * inv4pi;
             double *Bs = sw + Z::B, *Bds = sw + Z::BD;
             const double B0 = fct * (Ib0 + G0.y), B1 = fct * (Ib1 + G1.y), B2 = fct * (Ib2 + G2.y), B3 = fct * (Ib3 + G3.y);
-            Bs[4 * lm] = B0;
-            Bs[4 * lm + 1] = B1;
-            Bs[4 * lm + 2] = B2;
-            Bs[4 * lm + 3] = B3;
-            {
-                // (0, nu') B, whose product with the S' fit gives the S' row (eq. sprime1formrep)
-                const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
+            // (0, nu') B, whose product with the S' fit gives the S' row (eq. sprime1formrep)
+            const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
+            const double Bp0 = n0 * B1 + n1 * B2 + n2 * B3, Bp1 = B0 * n0 + (n1 * B3 - n2 * B2);
+            const double Bp2 = B0 * n1 + (n2 * B1 - n0 * B3), Bp3 = B0 * n2 + (n0 * B2 - n1 * B1);
+            const double psi = fct * (Ip + St[jk_index(l, m)].y * Om[0]);
+            if (MIX) {
+                // rows in double-float: the row phase reads (hi, lo) pairs in the same slots
+                float2 *Bf = reinterpret_cast<float2 *>(Bs) + 4 * lm, *Bpf = reinterpret_cast<float2 *>(sw + Z::DQ) + 4 * lm;
+                Bf[0] = split2d(B0); Bf[1] = split2d(B1); Bf[2] = split2d(B2); Bf[3] = split2d(B3);
+                Bpf[0] = split2d(Bp0); Bpf[1] = split2d(Bp1); Bpf[2] = split2d(Bp2); Bpf[3] = split2d(Bp3);
+                reinterpret_cast<float2 *>(sw + Z::PSI)[lm] = split2d(psi);
+            } else {
+                Bs[4 * lm] = B0; Bs[4 * lm + 1] = B1; Bs[4 * lm + 2] = B2; Bs[4 * lm + 3] = B3;
                 double *Bp = sw + Z::DQ + 4 * lm;
-                Bp[0] = n0 * B1 + n1 * B2 + n2 * B3;
-                Bp[1] = B0 * n0 + (n1 * B3 - n2 * B2);
-                Bp[2] = B0 * n1 + (n2 * B1 - n0 * B3);
-                Bp[3] = B0 * n2 + (n0 * B2 - n1 * B1);
+                Bp[0] = Bp0; Bp[1] = Bp1; Bp[2] = Bp2; Bp[3] = Bp3;
+                sw[Z::PSI + lm] = psi;
             }
-            sw[Z::PSI + lm] = fct * (Ip + St[jk_index(l, m)].y * Om[0]);
             if (wantDP) {
                 const double X0 = Om[4], X1 = Om[5], X2 = Om[6], X3 = Om[7];
                 const cd E0 = cscale(cadd(cadd(cscale(g[0], X1), cscale(g[1], X2)), cscale(g[2], X3)), -1.0);
@@ -662,10 +766,14 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const cd F1 = cadd(cscale(hn[0], W0), csub(cscale(hn[2], W2), cscale(hn[1], W3)));
                 const cd F2 = cadd(cscale(hn[1], W0), csub(cscale(hn[0], W3), cscale(hn[2], W1)));
                 const cd F3 = cadd(cscale(hn[2], W0), csub(cscale(hn[1], W1), cscale(hn[0], W2)));
-                Bds[4 * lm] = fct * (dI0 + E0.y + F0.y);
-                Bds[4 * lm + 1] = fct * (dI1 + E1.y + F1.y);
-                Bds[4 * lm + 2] = fct * (dI2 + E2.y + F2.y);
-                Bds[4 * lm + 3] = fct * (dI3 + E3.y + F3.y);
+                const double d0 = fct * (dI0 + E0.y + F0.y), d1 = fct * (dI1 + E1.y + F1.y);
+                const double d2 = fct * (dI2 + E2.y + F2.y), d3 = fct * (dI3 + E3.y + F3.y);
+                if (MIX) {
+                    float2 *Bdf = reinterpret_cast<float2 *>(Bds) + 4 * lm;
+                    Bdf[0] = split2d(d0); Bdf[1] = split2d(d1); Bdf[2] = split2d(d2); Bdf[3] = split2d(d3);
+                } else {
+                    Bds[4 * lm] = d0; Bds[4 * lm + 1] = d1; Bds[4 * lm + 2] = d2; Bds[4 * lm + 3] = d3;
+                }
             }
         }
         __syncthreads();
@@ -679,7 +787,49 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const double *fr = sw + Z::FR;
             const double sc = fr[12];
             double r0 = 0, r1 = 0;  // group 0: D, D'; group 1: S'; group 2: S
-            if (grp == 0) {
+            if (MIX) {
+                // double-float dot products with the (hi, lo) fit matrices
+                dfa a0 = {0, 0}, a1 = {0, 0};
+                if (grp == 0) {
+                    const float2 *X = pd.XD2 + ps * pd_X();
+                    const float2 *Bf = reinterpret_cast<const float2 *>(sw + Z::B), *Bdf = reinterpret_cast<const float2 *>(sw + Z::BD);
+                    for (int lm = 0; lm < NP; lm++) {
+                        const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
+                        const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
+                        const float2 b0 = Bf[4 * lm], b1 = Bf[4 * lm + 1], b2 = Bf[4 * lm + 2], b3 = Bf[4 * lm + 3];
+                        dfmac(a0, -b0.x, -b0.y, x0.x, x0.y); dfmac(a0, b1.x, b1.y, x1.x, x1.y);
+                        dfmac(a0, b2.x, b2.y, x2.x, x2.y); dfmac(a0, b3.x, b3.y, x3.x, x3.y);
+                        if (wantDP) {
+                            const float2 c0 = Bdf[4 * lm], c1 = Bdf[4 * lm + 1], c2 = Bdf[4 * lm + 2], c3 = Bdf[4 * lm + 3];
+                            dfmac(a1, -c0.x, -c0.y, x0.x, x0.y); dfmac(a1, c1.x, c1.y, x1.x, x1.y);
+                            dfmac(a1, c2.x, c2.y, x2.x, x2.y); dfmac(a1, c3.x, c3.y, x3.x, x3.y);
+                        }
+                    }
+                    r0 = dfval(a0);
+                    r1 = dfval(a1) * sc;
+                } else if (grp == 1) {
+                    const float2 *X = pd.XSp2 + ps * pd_X(), *Bpf = reinterpret_cast<const float2 *>(sw + Z::DQ);
+                    for (int lm = 0; lm < NP; lm++)
+                        for (int c = 0; c < 4; c++) {
+                            const float2 x = X[(c * NP + lm) * NP + i], b = Bpf[4 * lm + c];
+                            dfmac(a0, b.x, b.y, x.x, x.y);
+                        }
+                    r0 = dfval(a0);
+                } else {
+                    const float2 *X = pd.XS22 + ps * pd_X(), *X1 = pd.XS12 + ps * pd_XS1();
+                    const float2 *Bf = reinterpret_cast<const float2 *>(sw + Z::B), *Pf = reinterpret_cast<const float2 *>(sw + Z::PSI);
+                    for (int lm = 0; lm < NP; lm++) {
+                        const float2 x1 = X1[lm * NP + i], ps_ = Pf[lm];
+                        dfmac(a0, ps_.x, ps_.y, x1.x, x1.y);
+                        const float2 b0 = Bf[4 * lm], b1 = Bf[4 * lm + 1], b2 = Bf[4 * lm + 2], b3 = Bf[4 * lm + 3];
+                        const float2 g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
+                        const float2 g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
+                        dfmac(a0, -b0.x, -b0.y, g0.x, g0.y); dfmac(a0, b1.x, b1.y, g1.x, g1.y);
+                        dfmac(a0, b2.x, b2.y, g2.x, g2.y); dfmac(a0, b3.x, b3.y, g3.x, g3.y);
+                    }
+                    r0 = dfval(a0) * (1.0 / sc);
+                }
+            } else if (grp == 0) {
                 const double *X = pd.XD + ps * pd_X(), *Bs = sw + Z::B, *Bds = sw + Z::BD;
                 for (int lm = 0; lm < NP; lm++) {
                     const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];

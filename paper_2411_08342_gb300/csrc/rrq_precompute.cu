@@ -17,6 +17,12 @@
 namespace {
 
 // complex double -> (re.hi, re.lo, im.hi, im.lo) as float pairs (about 48 bits)
+// x as (hi, lo) float pair
+__device__ __forceinline__ float2 split2f(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
 __device__ __forceinline__ float4 split4(cd v) {
     const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
     return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
@@ -434,8 +440,17 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         double s = 0;
         for (int k = 0; k < NP; k++) s += W[4 * (lm * 2 * NP + k) + comp] * TMP[k * NP + i];
         gXS2[w] = s;
+        if (pd.XD2) {
+            const size_t o2 = (size_t)pid * pd_X() + w;
+            pd.XD2[o2] = split2f(qd[comp]);
+            pd.XSp2[o2] = split2f(qs[comp]);
+            pd.XS22[o2] = split2f(s);
+        }
     }
-    for (int w = tid; w < NP * NP; w += nth) gXS1[w] = ASI[w];
+    for (int w = tid; w < NP * NP; w += nth) {
+        gXS1[w] = ASI[w];
+        if (pd.XS12) pd.XS12[(size_t)pid * pd_XS1() + w] = split2f(ASI[w]);
+    }
     if (tid == 0) pd.status[pid] = s_bad;
 }
 
