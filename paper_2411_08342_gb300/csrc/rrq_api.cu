@@ -182,11 +182,6 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     rrq_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.ptilde != 0) {
-        bool ok = true;
-        for (int p = 2; p <= RRQ_PMAX; p++) (void)p;
-        if (!ok) return RRQ_ERR_UNSUPPORTED;
-    }
     const double eta = o.eta > 0 ? o.eta : 1.0;
     const int newton_max = o.newton_max > 0 ? o.newton_max : 30;
     CK(cudaSetDevice(ctx->device));

@@ -228,10 +228,9 @@ cudaError_t rrq_scan_exclusive(const int64_t *in, int64_t *out, int64_t n, int64
     if (e != cudaSuccess) return e;
     if (nb > 1) {
         e = rrq_scan_exclusive(bsum, boff, nb, tmp + 2 * nb + 2, st);
-        if (e != cudaSuccess) return e; {
+        if (e != cudaSuccess) return e;
         k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(out, n, boff);
         RRQ_COUNT_LAUNCH();
-    }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         // total = boff[nb]
@@ -271,10 +270,9 @@ cudaError_t rrq_near_build(const double *d_bounds, int npatch, const int64_t *d_
     for (int a = 0; a < 3; a++) { init[1 + a] = ~0ULL; init[4 + a] = 0ULL; }
     init[7] = 0ULL;
     cudaError_t e = cudaMemcpyAsync(red, init, sizeof(init), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e; {
+    if (e != cudaSuccess) return e;
     k_patch_reach<<<(npatch + 255) / 256, 256, 0, st>>>(d_bounds, npatch, eta, red);
     RRQ_COUNT_LAUNCH();
-}
     unsigned long long hred[8];
     e = cudaMemcpyAsync(hred, red, sizeof(hred), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
@@ -318,10 +316,9 @@ cudaError_t rrq_near_build(const double *d_bounds, int npatch, const int64_t *d_
         rrq_widen_int<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(cell_cnt, wide, (int64_t)ncell);
         RRQ_COUNT_LAUNCH();
         e = rrq_scan_exclusive(wide, wscan, (int64_t)ncell, scan_tmp, st);
-        if (e != cudaSuccess) return e; {
+        if (e != cudaSuccess) return e;
         rrq_narrow_int<<<(unsigned)((ncell + 1 + 255) / 256), 256, 0, st>>>(wscan, cell_cnt, (int64_t)ncell + 1);
         RRQ_COUNT_LAUNCH();
-    }
     }
     int *cursor = (int *)alloc(actx, sizeof(int) * (ncell + 1));
     if (!cursor) return cudaErrorMemoryAllocation;
@@ -374,8 +371,10 @@ cudaError_t rrq_items_build(const NearBuffers *nb, int64_t ntarg, const int32_t 
     PairItem *items = (PairItem *)alloc(actx, sizeof(PairItem) * (nb->npairs > 0 ? nb->npairs : 1));
     if (!rowlen || !scan_tmp || !rcnt || !roff || !items) return cudaErrorMemoryAllocation;
     unsigned tb = (unsigned)((ntarg + 127) / 128);
-    if (ntarg > 0) k_row_len<<<tb, 128, 0, st>>>(nb->poff, nb->pairs, ntarg, d_order, rowlen);
-    RRQ_COUNT_LAUNCH();
+    if (ntarg > 0) {
+        k_row_len<<<tb, 128, 0, st>>>(nb->poff, nb->pairs, ntarg, d_order, rowlen);
+        RRQ_COUNT_LAUNCH();
+    }
     cudaError_t e = rrq_scan_exclusive(rowlen, d_rowptr, ntarg, scan_tmp, st);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(rcnt, 0, sizeof(int64_t) * (npatch + 1), st);
@@ -387,8 +386,10 @@ cudaError_t rrq_items_build(const NearBuffers *nb, int64_t ntarg, const int32_t 
     if (e != cudaSuccess) return e;
     int64_t *cursor = rcnt;  // reuse
     cudaMemcpyAsync(cursor, roff, sizeof(int64_t) * (npatch + 1), cudaMemcpyDeviceToDevice, st);
-    if (ntarg > 0) k_items<<<tb, 128, 0, st>>>(nb->poff, nb->pairs, ntarg, d_order, d_rowptr, d_rank, cursor, items);
-    RRQ_COUNT_LAUNCH();
+    if (ntarg > 0) {
+        k_items<<<tb, 128, 0, st>>>(nb->poff, nb->pairs, ntarg, d_order, d_rowptr, d_rank, cursor, items);
+        RRQ_COUNT_LAUNCH();
+    }
     *items_out = items;
     *rank_off_out = roff;
     return cudaGetLastError();

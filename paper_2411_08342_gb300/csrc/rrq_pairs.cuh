@@ -75,6 +75,14 @@ __device__ __forceinline__ cd sqrt_c(cd z) {
     return mkc(re, z.y < 0 ? -im : im);
 }
 
+// 1/n for n = 0 .. 2 RRQ_PMAX + 1 (entry 0 unused)
+__device__ __forceinline__ double rcp_small(int n) {
+    constexpr double R[2 * RRQ_PMAX + 2] = {0.0,       1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,
+                                            1.0 / 6,   1.0 / 7,    1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11,
+                                            1.0 / 12,  1.0 / 13,   1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17};
+    return R[n];
+}
+
 // Table of Rn_n^q (0 <= q <= n <= P), column m = lane computed by the warp.
 template <int P>
 __device__ __forceinline__ void target_table(const double *y, cd *S, int lane) {
@@ -82,11 +90,11 @@ __device__ __forceinline__ void target_table(const double *y, cd *S, int lane) {
         const double X = y[1], Y = y[2], Z = y[0], r2 = X * X + Y * Y + Z * Z;
         const int m = lane;
         cd w = mkc(1.0, 0.0);
-        for (int k = 1; k <= m; k++) w = cscale(cmul(w, mkc(X, Y)), 1.0 / (2.0 * k));
+        for (int k = 1; k <= m; k++) w = cscale(cmul(w, mkc(X, Y)), 0.5 * rcp_small(k));
         cd prev = mkc(0.0, 0.0), cur = w;
         S[jk_index(m, m)] = cur;
         for (int l = m; l < P; l++) {
-            cd nxt = cscale(csub(cscale(cur, (2.0 * l + 1.0) * Z), cscale(prev, r2)), 1.0 / ((l - m + 1.0) * (l + m + 1.0)));
+            cd nxt = cscale(csub(cscale(cur, (2.0 * l + 1.0) * Z), cscale(prev, r2)), rcp_small(l - m + 1) * rcp_small(l + m + 1));
             S[jk_index(l + 1, m)] = nxt;
             prev = cur;
             cur = nxt;

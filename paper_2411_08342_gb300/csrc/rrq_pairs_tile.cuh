@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 J[1] = (sp - sm) + a * J[0];
                 for (int i = 2; i < PT; i++) {
                     const double br = ((i - 1) & 1) ? sp + sm : sp - sm;
-                    J[i] = (br + (2.0 * i - 1.0) * a * J[i - 1] - (i - 1.0) * c0 * J[i - 2]) / i;
+                    J[i] = (br + (2.0 * i - 1.0) * a * J[i - 1] - (i - 1.0) * c0 * J[i - 2]) * rcp_small(i);
                 }
                 if (wantDP) {
                     K[0] = ((1 - a) / sp + (1 + a) / sm) / (bi * bi);
