@@ -250,6 +250,7 @@ def bench_gpu(args):
     # kernel launches per step: per-order precompute and pair kernels, near list, scans, items
     launches = diag.get("kernel_launches", None)
     apply = None if args.no_apply else apply_leg(ctx, surf, targ, d, tg, dev)
+    evaluate = None if args.no_apply else evaluate_leg(ctx, surf, targ, d, tg, dev, ms_step)
     batched = None if (args.no_batched or world > 1) else batched_leg(ctx, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -270,6 +271,7 @@ def bench_gpu(args):
         "gpu_launches": launches * args.steps if launches is not None else None,
         "points_per_s": world * tg.n / (ms_step * 1e-3),
         "apply": apply,
+        "evaluate_near": evaluate,
         "batched": batched,
         "mixed": {"value": total_entries / (ms_mixed * 1e-3), "unit": UNIT, "ms_per_step": ms_mixed,
                   "stage_ms": {"precompute": mdiag["ms_precompute"], "near_and_items": mdiag["ms_near"],
@@ -335,6 +337,30 @@ def apply_leg(ctx, surf, targ, d, tg, dev, reps: int = 3) -> dict:
                             "max_rel_diff_vs_fp64_apply": max(rel32),
                             "precision": "smooth terms beyond r_c in FP32 (hi/lo coordinates, compensated tile "
                                          "sums), closer ones in FP64 inside the correction SpMV"}}
+
+
+def evaluate_leg(ctx, surf, targ, d, tg, dev, ms_build: float, reps: int = 3) -> dict:
+    """Density-given near evaluation (rrq_evaluate_near, all four kernels): the correction
+    applied to a density without the matrix; timed by CUDA events around the call,
+    against building the four CSRs (the FP64 step time)."""
+    import torch
+    sig = torch.as_tensor(np.random.default_rng(SEED + 9).standard_normal(d.nnode), dtype=torch.float64, device=dev)
+    outs = {k: torch.empty(tg.n, dtype=torch.float64, device=dev) for k in KERNELS}
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for it in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.evaluate_near(surf, targ, sig, outs)
+        e1.record(stream)
+        e1.synchronize()
+        if it > 0:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    npairs = ctx.diagnostics()["npairs"]
+    return {"ms": ms, "targets_per_s": tg.n / (ms * 1e-3), "pairs_per_s": npairs / (ms * 1e-3),
+            "speedup_vs_matrix_build": ms_build / ms,
+            "note": "S, D, S', D' corrections applied to a random density, no CSR stored"}
 
 
 def batched_leg(ctx, dev) -> dict:

@@ -166,6 +166,19 @@ rrq_status rrq_csr_free(rrq_ctx *ctx, rrq_csr *csr);
 rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, int32_t kernel,
                      const rrq_csr *corr, const double *density, double *out, const rrq_options *opt);
 
+/* Density-given near evaluation (Sec. 4 Steps 1-8 with Step 2 for a given density, as the
+ * paper evaluates close targets without storing the matrix):
+ *     out[k][t] = sum_j C_k[t][j] density[j]        for every kernel k in kernel_mask
+ * i.e. the correction of rrq_build_corrections applied to `density`, computed without the
+ * CSR: per patch the fit coefficients X sigma are formed once, then per (target, patch)
+ * pair only the B . (X sigma) products (O(p^2) per pair instead of O(p^4)), the jump and
+ * the smooth rule.  out[k] ([ntarg], device or host as inputs_on_host; indexed S, D, S',
+ * D') must be non-NULL for every requested kernel.  FP64 only (precision = 1 gives
+ * RRQ_ERR_UNSUPPORTED).  The smooth sum over all nodes is not included: rrq_apply with a
+ * NULL CSR gives it.  Synchronises the context stream; diagnostics as for a build. */
+rrq_status rrq_evaluate_near(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, uint32_t kernel_mask,
+                             const double *density, double *out[4], const rrq_options *opt);
+
 /* Counters and stage timings of the last rrq_build_corrections on this context. */
 rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag);
 

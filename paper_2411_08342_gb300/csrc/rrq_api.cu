@@ -20,7 +20,8 @@ void set_err(const char *what, cudaError_t e) { snprintf(g_err, RRQ_ERR_LEN, "%s
 
 #define RRQ_DECL_PAIRS(P)                                                                              \
     cudaError_t rrq_launch_pairs_p##P(bool, const PairArgs &, const PairShape &, cudaStream_t); \
-    int rrq_pair_tiles_p##P(int out[4]);
+    int rrq_pair_tiles_p##P(int out[4]);                                                                  \
+    cudaError_t rrq_launch_pairs_eval_p##P(const PairArgs &, const PairShape &, cudaStream_t);
 RRQ_DECL_PAIRS(2)
 RRQ_DECL_PAIRS(3)
 RRQ_DECL_PAIRS(4)
@@ -34,6 +35,16 @@ cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape sha
     switch (p) {
 #define RRQ_CASE(P) \
     case P: return rrq_launch_pairs_p##P(mixed, a, shape, st);
+        RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
+#undef RRQ_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t rrq_launch_pairs_eval(int p, const PairArgs &a, PairShape shape, cudaStream_t st) {
+    switch (p) {
+#define RRQ_CASE(P) \
+    case P: return rrq_launch_pairs_eval_p##P(a, shape, st);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
 #undef RRQ_CASE
         default: return cudaErrorInvalidValue;
@@ -174,22 +185,33 @@ rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag) {
 }  // extern "C"
 
 
-extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
-                                            uint32_t kernel_mask, const rrq_options *opt, rrq_csr *out) {
-    if (!ctx || !out) return RRQ_ERR_ARG;
-    memset(out, 0, sizeof(*out));
-    if (kernel_mask == 0 || (kernel_mask & ~15u)) return RRQ_ERR_ARG;
-    rrq_options o;
-    memset(&o, 0, sizeof(o));
-    if (opt) o = *opt;
-    const double eta = o.eta > 0 ? o.eta : 1.0;
-    const int newton_max = o.newton_max > 0 ? o.newton_max : 30;
-    CK(cudaSetDevice(ctx->device));
-    memset(&ctx->diag, 0, sizeof(ctx->diag));
-    rrq_launch_counter() = 0;
-    Scratch s;
-    s.st = ctx->stream;
+namespace {
+
+// Everything a build needs before the per-pair stage: device inputs, per-order tables,
+// per-patch data (Steps 1-3, precompute kernels), near list and pair items grouped by
+// (order, patch), CSR row pointers and entry count.  Stage times go to ctx->diag.
+struct Prep {
     Inputs in;
+    std::vector<std::vector<int32_t>> plist;
+    PatchData pd{};
+    NearBuffers nb{};
+    int64_t *rowptr = nullptr;  // [ntarg + 1]; cudaMallocAsync'd when rowptr_for_caller, else scratch
+    PairItem *items = nullptr;
+    std::vector<int64_t> h_roff;
+    int64_t nnz = 0;
+    BuildCounters *d_cnt = nullptr;
+    bool mixed = false;
+    int newton_max = 30;
+};
+
+rrq_status build_prep(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const rrq_targets *targ, const rrq_options &o,
+                      bool rowptr_for_caller, Prep &pr) {
+    const double eta = o.eta > 0 ? o.eta : 1.0;
+    pr.newton_max = o.newton_max > 0 ? o.newton_max : 30;
+    if (o.precision != 0 && o.precision != 1) return RRQ_ERR_ARG;
+    pr.mixed = o.precision == 1;
+    const bool mixed = pr.mixed;
+    Inputs &in = pr.in;
     rrq_status rs = prepare_inputs(ctx, s, surf, targ, o.inputs_on_host != 0, true, in);
     if (rs != RRQ_OK) return rs;
     if (o.ptilde != 0)
@@ -197,7 +219,8 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
             if (o.ptilde != 2 * in.h_order[P]) return RRQ_ERR_UNSUPPORTED;
     // per-order tables and patch lists
     int pmax = 0;
-    std::vector<std::vector<int32_t>> plist(RRQ_PMAX + 1);
+    std::vector<std::vector<int32_t>> &plist = pr.plist;
+    plist.assign(RRQ_PMAX + 1, {});
     for (int P = 0; P < in.npatch; P++) {
         plist[in.h_order[P]].push_back(P);
         pmax = std::max(pmax, in.h_order[P]);
@@ -209,7 +232,7 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
         }
     // patch data
     const size_t NPc = in.npatch;
-    PatchData pd{};
+    PatchData &pd = pr.pd;
     pd.npatch = in.npatch;
     pd.pmax = pmax;
     pd.frame = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_FRAME);
@@ -222,8 +245,6 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     pd.eyu = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_eyu());
     pd.eg = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
     pd.eh = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
-    const bool mixed = o.precision == 1;
-    if (o.precision != 0 && o.precision != 1) return RRQ_ERR_ARG;
     pd.eg2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
     pd.eh2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
     if (mixed) {
@@ -245,11 +266,11 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     for (int r = 0; r < in.npatch; r++) rank[order_major[r]] = r;
     int32_t *d_plists = (int32_t *)Scratch::alloc(&s, sizeof(int32_t) * in.npatch);
     int32_t *d_rank = (int32_t *)Scratch::alloc(&s, sizeof(int32_t) * in.npatch);
-    BuildCounters *d_cnt = (BuildCounters *)Scratch::alloc(&s, sizeof(BuildCounters));
+    pr.d_cnt = (BuildCounters *)Scratch::alloc(&s, sizeof(BuildCounters));
     if (s.failed) return RRQ_ERR_OOM;
     CK(cudaMemcpyAsync(d_plists, order_major.data(), sizeof(int32_t) * in.npatch, cudaMemcpyHostToDevice, s.st));
     CK(cudaMemcpyAsync(d_rank, rank.data(), sizeof(int32_t) * in.npatch, cudaMemcpyHostToDevice, s.st));
-    CK(cudaMemsetAsync(d_cnt, 0, sizeof(BuildCounters), s.st));
+    CK(cudaMemsetAsync(pr.d_cnt, 0, sizeof(BuildCounters), s.st));
     CK(cudaEventRecord(ctx->ev[0], s.st));
     {
         int start = 0;
@@ -260,35 +281,67 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
         }
     }
     CK(cudaEventRecord(ctx->ev[1], s.st));
-    NearBuffers nb;
-    CK(rrq_near_build(pd.bounds, in.npatch, in.node_off, in.txyz, in.tself, in.ntarg, eta, &Scratch::alloc, &s, &nb,
+    CK(rrq_near_build(pd.bounds, in.npatch, in.node_off, in.txyz, in.tself, in.ntarg, eta, &Scratch::alloc, &s, &pr.nb,
                       s.st));
     if (s.failed) return RRQ_ERR_OOM;
-    int64_t *d_rowptr = nullptr;
-    CK(cudaMallocAsync(&d_rowptr, sizeof(int64_t) * (in.ntarg + 1), s.st));
-    PairItem *items = nullptr;
+    if (rowptr_for_caller)
+        CK(cudaMallocAsync(&pr.rowptr, sizeof(int64_t) * (in.ntarg + 1), s.st));
+    else
+        pr.rowptr = (int64_t *)Scratch::alloc(&s, sizeof(int64_t) * (in.ntarg + 1));
+    if (!pr.rowptr) return RRQ_ERR_OOM;
     int64_t *roff = nullptr;
-    cudaError_t e = rrq_items_build(&nb, in.ntarg, in.order, d_rank, in.npatch, &Scratch::alloc, &s, d_rowptr, &items,
-                                    &roff, s.st);
+    cudaError_t e = rrq_items_build(&pr.nb, in.ntarg, in.order, d_rank, in.npatch, &Scratch::alloc, &s, pr.rowptr,
+                                    &pr.items, &roff, s.st);
     if (e != cudaSuccess || s.failed) {
-        cudaFreeAsync(d_rowptr, s.st);
         set_err("pair items", e);
         return s.failed ? RRQ_ERR_OOM : RRQ_ERR_CUDA;
     }
     // sizes: nnz and the item range of every order
-    int64_t nnz = 0;
-    std::vector<int64_t> h_roff(in.npatch + 1);
-    CK(cudaMemcpyAsync(&nnz, d_rowptr + in.ntarg, sizeof(int64_t), cudaMemcpyDeviceToHost, s.st));
-    CK(cudaMemcpyAsync(h_roff.data(), roff, sizeof(int64_t) * (in.npatch + 1), cudaMemcpyDeviceToHost, s.st));
+    pr.h_roff.assign(in.npatch + 1, 0);
+    CK(cudaMemcpyAsync(&pr.nnz, pr.rowptr + in.ntarg, sizeof(int64_t), cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(pr.h_roff.data(), roff, sizeof(int64_t) * (in.npatch + 1), cudaMemcpyDeviceToHost, s.st));
     std::vector<int> h_status(in.npatch);
     CK(cudaMemcpyAsync(h_status.data(), pd.status, sizeof(int) * in.npatch, cudaMemcpyDeviceToHost, s.st));
     CK(cudaEventRecord(ctx->ev[2], s.st));
     CK(cudaStreamSynchronize(s.st));
     for (int P = 0; P < in.npatch; P++)
-        if (h_status[P]) {
-            cudaFreeAsync(d_rowptr, s.st);
-            return RRQ_ERR_DEGENERATE;
-        }
+        if (h_status[P]) return RRQ_ERR_DEGENERATE;
+    return RRQ_OK;
+}
+
+}  // namespace
+
+extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
+                                            uint32_t kernel_mask, const rrq_options *opt, rrq_csr *out) {
+    if (!ctx || !out) return RRQ_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    if (kernel_mask == 0 || (kernel_mask & ~15u)) return RRQ_ERR_ARG;
+    rrq_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    CK(cudaSetDevice(ctx->device));
+    memset(&ctx->diag, 0, sizeof(ctx->diag));
+    rrq_launch_counter() = 0;
+    Scratch s;
+    s.st = ctx->stream;
+    Prep pr;
+    rrq_status rs = build_prep(ctx, s, surf, targ, o, true, pr);
+    if (rs != RRQ_OK) {
+        if (pr.rowptr) cudaFreeAsync(pr.rowptr, s.st);
+        return rs;
+    }
+    const Inputs &in = pr.in;
+    const std::vector<std::vector<int32_t>> &plist = pr.plist;
+    const PatchData &pd = pr.pd;
+    const NearBuffers &nb = pr.nb;
+    int64_t *d_rowptr = pr.rowptr;
+    PairItem *items = pr.items;
+    const std::vector<int64_t> &h_roff = pr.h_roff;
+    const int64_t nnz = pr.nnz;
+    BuildCounters *d_cnt = pr.d_cnt;
+    const bool mixed = pr.mixed;
+    const int newton_max = pr.newton_max;
+    cudaError_t e = cudaSuccess;
     int32_t *col = nullptr;
     double *vals[4] = {nullptr, nullptr, nullptr, nullptr};
     bool oom = cudaMallocAsync(&col, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s.st) != cudaSuccess;
@@ -375,6 +428,134 @@ __global__ void k_rebase(int64_t *rowptr, int64_t n, int64_t first) {
     if (i < n) rowptr[i] -= first;
 }
 }  // namespace
+
+namespace {
+
+// Fit coefficients of the density on every patch (Sec. 4 Step 2 for a given density):
+// [P][13 NPMAX] = X_D sigma_P (4 n_p rows), X_S' sigma_P, X_S2 sigma_P, X_S1 sigma_P (n_p rows).
+__global__ void k_patch_coef(const int32_t *__restrict__ order, const int64_t *__restrict__ node_off, PatchData pd,
+                             const double *__restrict__ sig, double *__restrict__ coef) {
+    const int P = blockIdx.x;
+    const int p = order[P], np = p * (p + 1) / 2;
+    const double *s = sig + node_off[P];
+    double *c = coef + (size_t)P * (13 * RRQ_NPMAX);
+    for (int r = threadIdx.x; r < 13 * np; r += blockDim.x) {
+        const double *X;
+        double *dst;
+        int row;
+        if (r < 12 * np) {
+            const int blk = r / (4 * np);
+            row = r % (4 * np);
+            X = (blk == 0 ? pd.XD : blk == 1 ? pd.XSp : pd.XS2) + (size_t)P * pd_X();
+            dst = c + blk * 4 * RRQ_NPMAX;
+        } else {
+            row = r - 12 * np;
+            X = pd.XS1 + (size_t)P * pd_XS1();
+            dst = c + 12 * RRQ_NPMAX;
+        }
+        double v = 0.0;
+        for (int i = 0; i < np; i++) v = fma(X[row * np + i], s[i], v);
+        dst[row] = v;
+    }
+}
+
+// out[t] = sum of the pair results of target t, in near-list order
+__global__ void k_pair_reduce(const int64_t *__restrict__ poff, int64_t ntarg, const double *__restrict__ res,
+                              double *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntarg) return;
+    double v = 0.0;
+    for (int64_t q = poff[t]; q < poff[t + 1]; q++) v += res[q];
+    out[t] = v;
+}
+
+}  // namespace
+
+extern "C" rrq_status rrq_evaluate_near(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
+                                        uint32_t kernel_mask, const double *density, double *out[4],
+                                        const rrq_options *opt) {
+    if (!ctx || !density || !out) return RRQ_ERR_ARG;
+    if (kernel_mask == 0 || (kernel_mask & ~15u)) return RRQ_ERR_ARG;
+    for (int k = 0; k < 4; k++)
+        if ((kernel_mask & (1u << k)) && !out[k]) return RRQ_ERR_ARG;
+    rrq_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.precision != 0) return RRQ_ERR_UNSUPPORTED;
+    CK(cudaSetDevice(ctx->device));
+    memset(&ctx->diag, 0, sizeof(ctx->diag));
+    rrq_launch_counter() = 0;
+    Scratch s;
+    s.st = ctx->stream;
+    Prep pr;
+    rrq_status rs = build_prep(ctx, s, surf, targ, o, false, pr);
+    if (rs != RRQ_OK) return rs;
+    const Inputs &in = pr.in;
+    const int64_t npairs = pr.nb.npairs;
+    if (npairs >= (int64_t)INT32_MAX) return RRQ_ERR_UNSUPPORTED;
+    const bool on_host = o.inputs_on_host != 0;
+    cudaError_t err = cudaSuccess;
+    const double *d_sig = upload(s, density, in.nnode, on_host, &err);
+    double *coef = (double *)Scratch::alloc(&s, sizeof(double) * (size_t)in.npatch * 13 * RRQ_NPMAX);
+    EdgeRoot *roots = (EdgeRoot *)Scratch::alloc(&s, sizeof(EdgeRoot) * 3 * (npairs > 0 ? npairs : 1));
+    int8_t *uside = (int8_t *)Scratch::alloc(&s, sizeof(int8_t) * (npairs > 0 ? npairs : 1));
+    unsigned long long *tile_ctr = (unsigned long long *)Scratch::alloc(&s, sizeof(unsigned long long) * (RRQ_PMAX + 1));
+    double *res[4] = {nullptr, nullptr, nullptr, nullptr}, *dout[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; k++)
+        if (kernel_mask & (1u << k)) {
+            res[k] = (double *)Scratch::alloc(&s, sizeof(double) * (npairs > 0 ? npairs : 1));
+            dout[k] = on_host ? (double *)Scratch::alloc(&s, sizeof(double) * (in.ntarg > 0 ? in.ntarg : 1)) : out[k];
+        }
+    if (err != cudaSuccess || s.failed) return RRQ_ERR_OOM;
+    k_patch_coef<<<in.npatch, 128, 0, s.st>>>(in.order, in.node_off, pr.pd, d_sig, coef);
+    RRQ_COUNT_LAUNCH();
+    CK(cudaGetLastError());
+    int start = 0;
+    for (int p = 2; p <= RRQ_PMAX; p++) {
+        const int n = (int)pr.plist[p].size();
+        if (n) {
+            const int64_t i0 = pr.h_roff[start], i1 = pr.h_roff[start + n];
+            PatchData pdo = pr.pd;
+            pdo.roots = roots + 3 * i0;
+            pdo.uside = uside + i0;
+            const PairArgs pa = {ctx->d_tab[p], pr.items + i0, i1 - i0, pdo, in.node_off, in.xyz, in.nrm, in.wts,
+                                 in.txyz, in.tnrm, in.tself, kernel_mask, pr.newton_max,
+                                 {nullptr, nullptr, nullptr, nullptr}, nullptr, pr.d_cnt,
+                                 coef, d_sig, {res[0], res[1], res[2], res[3]}};
+            CK(rrq_launch_pairs_eval(p, pa, PairShape{ctx->tune_tile[0][p], ctx->tune_pers[0][p], tile_ctr + p}, s.st));
+        }
+        start += n;
+    }
+    for (int k = 0; k < 4; k++)
+        if (res[k] && in.ntarg > 0) {
+            k_pair_reduce<<<(unsigned)((in.ntarg + 255) / 256), 256, 0, s.st>>>(pr.nb.poff, in.ntarg, res[k], dout[k]);
+            RRQ_COUNT_LAUNCH();
+            CK(cudaGetLastError());
+        }
+    CK(cudaEventRecord(ctx->ev[3], s.st));
+    if (on_host)
+        for (int k = 0; k < 4; k++)
+            if (dout[k] && in.ntarg > 0)
+                CK(cudaMemcpyAsync(out[k], dout[k], sizeof(double) * in.ntarg, cudaMemcpyDeviceToHost, s.st));
+    BuildCounters hc;
+    CK(cudaMemcpyAsync(&hc, pr.d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    ctx->diag.npairs = npairs;
+    ctx->diag.newton_fail = (int64_t)hc.newton_fail;
+    ctx->diag.on_edge = (int64_t)hc.on_edge;
+    ctx->diag.u_poor = (int64_t)hc.u_poor;
+    ctx->diag.ssq_edges = (int64_t)hc.ssq_edges;
+    ctx->diag.far_edges = (int64_t)hc.far_edges;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    ctx->diag.ms_precompute = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    ctx->diag.ms_near = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    ctx->diag.ms_pairs = ms;
+    ctx->diag.kernel_launches = rrq_launch_counter();
+    return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
+}
 
 extern "C" rrq_status rrq_csr_copy(rrq_ctx *ctx, const rrq_csr *csr, int64_t *rowptr, int32_t *col, double *val[4],
                                    int32_t dst_on_host) {

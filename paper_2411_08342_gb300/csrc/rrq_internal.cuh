@@ -101,7 +101,8 @@ __host__ __device__ __forceinline__ size_t pd_eg() { return (size_t)3 * RRQ_PTMA
 __host__ __device__ __forceinline__ size_t pd_X() { return (size_t)4 * RRQ_NPMAX * RRQ_NPMAX; }
 __host__ __device__ __forceinline__ size_t pd_XS1() { return (size_t)RRQ_NPMAX * RRQ_NPMAX; }
 
-// Pair work item: target, patch, offset of the first CSR entry of the pair.
+// Pair work item: target, patch, offset of the first CSR entry of the pair, and the
+// pair's index in target-major order (near-list order).
 struct PairItem {
     int64_t t;
     int64_t off;
@@ -138,6 +139,12 @@ struct PairArgs {
     double *val[4];       // S, D, S', D' values (NULL = not built)
     int32_t *col;
     BuildCounters *cnt;
+    // density-given evaluation (rrq_evaluate_near) instead of rows: per patch the fit
+    // coefficients of the density, [P][13 NPMAX] = X_D sigma (4 NPMAX), X_S' sigma, X_S2 sigma,
+    // X_S1 sigma (NPMAX); the density; one result per (pair in target-major order, kernel)
+    const double *coef;
+    const double *sigma;
+    double *res[4];
 };
 
 // Launch shape of the per-pair stage.
@@ -149,5 +156,8 @@ struct PairShape {
 
 // Roots and pair kernels of order p; mixed = line integrals in double-float (needs pd.eg2, pd.eh2).
 cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape shape, cudaStream_t st);
+// The same stage in density-given evaluation form (FP64, PairArgs.coef/sigma/res, item.pad =
+// the pair's index in target-major order).
+cudaError_t rrq_launch_pairs_eval(int p, const PairArgs &a, PairShape shape, cudaStream_t st);
 // Tile sizes compiled for order p (the first is the default); returns their number.
 int rrq_pair_tiles(int p, int tiles[4]);

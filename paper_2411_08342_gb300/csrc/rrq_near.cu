@@ -203,7 +203,7 @@ __global__ void k_items(const int64_t *__restrict__ poff, const int32_t *__restr
         it.t = t;
         it.off = o;
         it.P = P;
-        it.pad = 0;
+        it.pad = (int32_t)k;  // index of the pair in target-major order
         items[pos] = it;
         o += p * (p + 1) / 2;
     }

@@ -6,4 +6,8 @@ cudaError_t rrq_launch_pairs_p5(bool mixed, const PairArgs &a, const PairShape &
     return rrqk::launch_pairs_order<5, 6, 4, 3>(mixed, a, shape, st);
 }
 
+cudaError_t rrq_launch_pairs_eval_p5(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    return rrqk::launch_pairs_eval_order<5, 6, 4, 3>(a, shape, st);
+}
+
 int rrq_pair_tiles_p5(int out[4]) { return rrqk::tiles_of<6, 4, 3>(out); }

@@ -6,4 +6,8 @@ cudaError_t rrq_launch_pairs_p6(bool mixed, const PairArgs &a, const PairShape &
     return rrqk::launch_pairs_order<6, 6, 4, 3>(mixed, a, shape, st);
 }
 
+cudaError_t rrq_launch_pairs_eval_p6(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    return rrqk::launch_pairs_eval_order<6, 6, 4, 3>(a, shape, st);
+}
+
 int rrq_pair_tiles_p6(int out[4]) { return rrqk::tiles_of<6, 4, 3>(out); }

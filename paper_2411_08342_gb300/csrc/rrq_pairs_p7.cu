@@ -6,4 +6,8 @@ cudaError_t rrq_launch_pairs_p7(bool mixed, const PairArgs &a, const PairShape &
     return rrqk::launch_pairs_order<7, 4, 2>(mixed, a, shape, st);
 }
 
+cudaError_t rrq_launch_pairs_eval_p7(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    return rrqk::launch_pairs_eval_order<7, 4, 2>(a, shape, st);
+}
+
 int rrq_pair_tiles_p7(int out[4]) { return rrqk::tiles_of<4, 2>(out); }

@@ -92,7 +92,7 @@ __device__ __forceinline__ void kitem(int f, int nt, int &pl, int &jk) {
     }
 }
 
-template <int P, bool MIX, int T>
+template <int P, bool MIX, int T, bool EVAL>
 __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned long long *tile_ctr) {
     const OrderTables *__restrict__ tab = a.tab;
     const PairItem *__restrict__ items = a.items;
@@ -777,6 +777,61 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
         }
         __syncthreads();
+        // M (density-given evaluation, Step 8 for a given density): per pair the fit coefficients
+        // of the density against B, Bd, (0, nu')B, Psi, then the jump and the smooth rule over the
+        // patch's nodes; one warp per pair, one result per (pair, kernel)
+        if (EVAL) {
+            for (int pl = warp; pl < nt; pl += nwarp) {
+                const double *sw = SW(pl);
+                const PairItem im = s_item[pl];
+                const double *c = a.coef + (size_t)im.P * (13 * RRQ_NPMAX);
+                const double *cD = c, *cSp = c + 4 * RRQ_NPMAX, *cS2 = c + 8 * RRQ_NPMAX, *cS1 = c + 12 * RRQ_NPMAX;
+                const double *Bs = sw + Z::B, *Bds = sw + Z::BD, *Bp = sw + Z::DQ, *Psis = sw + Z::PSI;
+                double qD = 0, qDp = 0, qSp = 0, qS = 0;
+                for (int lm = lane; lm < NP; lm += 32) {
+                    const double B0 = Bs[4 * lm], B1 = Bs[4 * lm + 1], B2 = Bs[4 * lm + 2], B3 = Bs[4 * lm + 3];
+                    qD -= B0 * cD[lm] - B1 * cD[NP + lm] - B2 * cD[2 * NP + lm] - B3 * cD[3 * NP + lm];
+                    if (wantDP)
+                        qDp -= Bds[4 * lm] * cD[lm] - Bds[4 * lm + 1] * cD[NP + lm] - Bds[4 * lm + 2] * cD[2 * NP + lm] -
+                               Bds[4 * lm + 3] * cD[3 * NP + lm];
+                    qSp += Bp[4 * lm] * cSp[lm] + Bp[4 * lm + 1] * cSp[NP + lm] + Bp[4 * lm + 2] * cSp[2 * NP + lm] +
+                           Bp[4 * lm + 3] * cSp[3 * NP + lm];
+                    qS += Psis[lm] * cS1[lm] -
+                          (B0 * cS2[lm] - B1 * cS2[NP + lm] - B2 * cS2[2 * NP + lm] - B3 * cS2[3 * NP + lm]);
+                }
+                const double sc = sw[Z::FR + 12];
+                const int64_t o = node_off[im.P];
+                double mD = 0, mDp = 0, mSp = 0, mS = 0;
+                for (int i = lane; i < NP; i += 32) {
+                    const double sg = a.sigma[o + i];
+                    if (i == s_self[pl]) {
+                        mD -= 0.5 * sg;
+                        mSp += 0.5 * sg;
+                    } else {
+                        const double *xs = xyz + 3 * (o + i), *ns = nrm + 3 * (o + i);
+                        const double d0 = sw[Z::XT] - xs[0], d1 = sw[Z::XT + 1] - xs[1], d2 = sw[Z::XT + 2] - xs[2];
+                        const double gn0 = sw[Z::NT], gn1 = sw[Z::NT + 1], gn2 = sw[Z::NT + 2];
+                        const double r2 = d0 * d0 + d1 * d1 + d2 * d2, r = sqrt(r2), r3 = r2 * r;
+                        const double wk = wts[o + i] * inv4pi * sg;
+                        const double dns = d0 * ns[0] + d1 * ns[1] + d2 * ns[2];
+                        const double dnt = d0 * gn0 + d1 * gn1 + d2 * gn2;
+                        mS -= wk / r;
+                        mD -= wk * dns / r3;
+                        mSp += wk * dnt / r3;
+                        mDp -= wk * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) / r3 - 3.0 * dns * dnt / (r3 * r2));
+                    }
+                }
+                qD = warp_sum(qD); qDp = warp_sum(qDp); qSp = warp_sum(qSp); qS = warp_sum(qS);
+                mD = warp_sum(mD); mDp = warp_sum(mDp); mSp = warp_sum(mSp); mS = warp_sum(mS);
+                if (lane == 0) {
+                    const int64_t q = im.pad;
+                    if (a.res[0]) a.res[0][q] = qS * (1.0 / sc) + mS;
+                    if (a.res[1]) a.res[1][q] = qD + mD;
+                    if (a.res[2]) a.res[2][q] = qSp + mSp;
+                    if (a.res[3]) a.res[3][q] = qDp * sc + mDp;
+                }
+            }
+        } else
         // M: rows through the fit matrices (Step 8), jump and smooth subtraction; one thread per
         // (kernel group, pair, node), groups {D, D'} (X_D), {S'} (X_S'), {S} (X_S2, X_S1)
         for (int f = tid; f < nt * NP * ngrp; f += nth) {
@@ -1055,17 +1110,18 @@ __global__ void __launch_bounds__(128) k_uside(const PairItem *__restrict__ item
     pd.uside[n] = side;
 }
 
-template <int P, bool MIX, int T>
+template <int P, bool MIX, int T, bool EVAL = false>
 cudaError_t launch_pairs_tile(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
     constexpr int NTH = TileCfg<P>::THREADS;
     const size_t bytes = sizeof(double) * PairSm<P>::TOTAL * T;
-    cudaError_t e = cudaFuncSetAttribute(k_pairs_tile<P, MIX, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_pairs_tile<P, MIX, T, EVAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     if (a.nitems <= 0) return cudaSuccess;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX, T>, NTH, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX, T, EVAL>, NTH, bytes);
     if (per_sm < 1) per_sm = 1;
     k_roots<P><<<(unsigned)((a.nitems * 3 + 127) / 128), 128, 0, st>>>(a.tab, a.items, a.nitems, a.pd, a.txyz,
                                                                        a.newton_max);
@@ -1086,7 +1142,7 @@ cudaError_t launch_pairs_tile(const PairArgs &a, const PairShape &shape, cudaStr
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
     }
-    k_pairs_tile<P, MIX, T><<<(unsigned)grid, NTH, bytes, st>>>(a, ctr);
+    k_pairs_tile<P, MIX, T, EVAL><<<(unsigned)grid, NTH, bytes, st>>>(a, ctr);
     RRQ_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -1101,6 +1157,16 @@ cudaError_t launch_pairs_order(bool mixed, const PairArgs &a, const PairShape &s
                                  : launch_pairs_tile<P, false, Ts>(a, shape, st))
               : (void)0),
      ...);
+    return e;
+}
+
+// Density-given evaluation (FP64), with the tile sizes of the matrix build.
+template <int P, int... Ts>
+cudaError_t launch_pairs_eval_order(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
+    constexpr int tiles[] = {Ts...};
+    const int T = shape.tile ? shape.tile : tiles[0];
+    cudaError_t e = cudaErrorInvalidValue;
+    ((T == Ts ? (void)(e = launch_pairs_tile<P, false, Ts, true>(a, shape, st)) : (void)0), ...);
     return e;
 }
 

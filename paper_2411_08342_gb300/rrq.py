@@ -99,6 +99,8 @@ def load(build_if_needed: bool = True):
             L.rrq_batch_csr.argtypes = [C.c_void_p, C.c_int32, C.POINTER(CSR), C.c_void_p, C.c_void_p]
             L.rrq_batch_info_get.argtypes = [C.c_void_p, C.POINTER(BatchInfo)]
             L.rrq_batch_destroy.argtypes = [C.c_void_p]
+            L.rrq_evaluate_near.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS), C.c_uint32,
+                                            C.c_void_p, C.c_void_p * 4, C.POINTER(Options)]
             L.rrq_autotune.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS), C.c_uint32,
                                        C.POINTER(Options)]
             _lib = L
@@ -205,6 +207,20 @@ class Context:
               inputs_on_host: bool = False) -> "Batch":
         """Batch plan over several surfaces (rrq_batch_create); see Batch."""
         return Batch(self, surfs, targs, kernels, mixed, autotune, inputs_on_host)
+
+    def evaluate_near(self, surf: Surface, targ: TargetsS, density, outs: dict, inputs_on_host: bool = False):
+        """Correction applied to `density` without the matrix (rrq_evaluate_near); outs maps
+        kernel names to output arrays [ntarg] (torch CUDA tensors, or numpy with
+        inputs_on_host)."""
+        mask = 0
+        arr = (C.c_void_p * 4)()
+        for k, v in outs.items():
+            mask |= KERNEL_BITS[k]
+            arr[KERNEL_SLOT[k]] = _ptr(v).value
+        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, 0)
+        st = self.L.rrq_evaluate_near(self.h, C.byref(surf), C.byref(targ), mask, _ptr(density), arr, C.byref(opt))
+        _check(st, "rrq_evaluate_near")
+        return outs
 
     def autotune(self, surf: Surface, targ: TargetsS, kernels=("S", "D", "SP", "DP"), mixed: bool = False):
         """Measure the per-pair launch shapes on this problem and keep them in the context
