@@ -252,6 +252,7 @@ def bench_gpu(args):
     apply = None if args.no_apply else apply_leg(ctx, surf, targ, d, tg, dev)
     evaluate = None if args.no_apply else evaluate_leg(ctx, surf, targ, d, tg, dev, ms_step)
     batched = None if (args.no_batched or world > 1) else batched_leg(ctx, dev)
+    stell = None if (args.no_batched or world > 1) else stellarator_leg(ctx, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -273,6 +274,7 @@ def bench_gpu(args):
         "apply": apply,
         "evaluate_near": evaluate,
         "batched": batched,
+        "stellarator": stell,
         "mixed": {"value": total_entries / (ms_mixed * 1e-3), "unit": UNIT, "ms_per_step": ms_mixed,
                   "stage_ms": {"precompute": mdiag["ms_precompute"], "near_and_items": mdiag["ms_near"],
                                "pairs": mdiag["ms_pairs"]},
@@ -361,6 +363,50 @@ def evaluate_leg(ctx, surf, targ, d, tg, dev, ms_build: float, reps: int = 3) ->
     return {"ms": ms, "targets_per_s": tg.n / (ms * 1e-3), "pairs_per_s": npairs / (ms * 1e-3),
             "speedup_vs_matrix_build": ms_build / ms,
             "note": "S, D, S', D' corrections applied to a random density, no CSR stored"}
+
+
+def stellarator_leg(ctx, dev) -> dict:
+    """The stellarator of eq. stellarator (24 x 72 parameter cells, 3,456 patches, all nodes as
+    targets) at p = 4, 6, 8: points per second of an S-only and a D-only correction build
+    (N / T with N the number of nodes, the measure of the paper's throughput table; one
+    GB300 here, one CPU core there), and the relative max error of Green's identity
+    1/2 u = S[du/dn] - D[u] for u = 1/|x| through rrq_apply."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    from paper_2411_08342_gb300 import workloads as W
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "stellarator 24x72 cells (3456 patches), on-surface nodes"}
+    for p in (4, 6, 8):
+        d, tg = W.stellarator(p)
+        a = rrq.device_inputs(d, tg, device=str(dev))
+        surf = ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv)
+        targ = ctx.targets(a["txyz"], a["tnrm"], a["tself"])
+        row = {"points": d.nnode}
+        for k in ("S", "D"):
+            times = []
+            for it in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                csr = ctx.build_corrections(surf, targ, (k,))
+                e1.record(stream)
+                e1.synchronize()
+                ctx.csr_free(csr)
+                if it > 0:
+                    times.append(e0.elapsed_time(e1))
+            row[f"points_per_s_{k}"] = d.nnode / (min(times) * 1e-3)
+        x = d.xyz
+        r = np.linalg.norm(x, axis=1)
+        u = 1.0 / r
+        dudn = -np.einsum("ia,ia->i", x, d.nrm) / r ** 3
+        csr = ctx.build_corrections(surf, targ, ("S", "D"))
+        oS = torch.empty(tg.n, dtype=torch.float64, device=dev)
+        oD = torch.empty_like(oS)
+        ctx.apply(surf, targ, "S", csr, torch.as_tensor(dudn, device=dev), oS)
+        ctx.apply(surf, targ, "D", csr, torch.as_tensor(u, device=dev), oD)
+        ctx.csr_free(csr)
+        row["green_identity_rel_err"] = float(np.abs((oS - oD).cpu().numpy() - 0.5 * u).max() / u.max())
+        out[f"p{p}"] = row
+    return out
 
 
 def batched_leg(ctx, dev) -> dict:

@@ -252,6 +252,59 @@ def wavy_torus_surface(n_theta: int, n_phi: int, R=1.0, r0=0.35, amp=0.05) -> Su
     return Surface(f"torus{len(par)}", len(par), fmap, {"n_theta": n_theta, "n_phi": n_phi})
 
 
+# Stellarator of Sec. 5 (eq. stellarator): non-zero coefficients delta_{i,j}
+STELLARATOR_DELTA = {(-1, -1): 0.17, (-1, 0): 0.11, (0, 0): 1.0, (1, 0): 4.5, (2, 0): -0.25, (0, 1): 0.07,
+                     (2, 1): -0.45}
+
+
+def _stellarator_xyz(u, v):
+    x = y = z = 0.0
+    for (i, j), dl in STELLARATOR_DELTA.items():
+        ang = (1 - i) * u + j * v
+        x = x + dl * np.cos(v) * np.cos(ang)
+        y = y + dl * np.sin(v) * np.cos(ang)
+        z = z + dl * np.sin(ang)
+    return np.stack([x, y, z], -1)
+
+
+def stellarator_surface(n_u: int, n_v: int) -> Surface:
+    """The stellarator r(u, v) of eq. stellarator on [0, 2 pi]^2, the parameter square cut
+    into n_u x n_v equal rectangles of two triangles each; triangles oriented so that
+    X_u x X_v points out of the enclosed volume."""
+    def build(flip):
+        cells = []
+        for i in range(n_u):
+            for j in range(n_v):
+                p00, p10, p01, p11 = (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)
+                if flip:
+                    cells += [(p00, p11, p10), (p00, p01, p11)]
+                else:
+                    cells += [(p00, p10, p11), (p00, p11, p01)]
+        par = np.array(cells, dtype=np.float64)
+        par[..., 0] *= 2 * math.pi / n_u
+        par[..., 1] *= 2 * math.pi / n_v
+
+        def fmap(idx, uv):
+            tr = par[idx]
+            a = tr[:, None, 0, :]
+            q = a + uv[..., 0:1] * (tr[:, None, 1, :] - a) + uv[..., 1:2] * (tr[:, None, 2, :] - a)
+            return _stellarator_xyz(q[..., 0], q[..., 1])
+        return Surface(f"stellarator{len(par)}", len(par), fmap, {"n_u": n_u, "n_v": n_v})
+    surf = build(False)
+    # enclosed volume by the divergence theorem, (1/3) int x . n dA, on a coarse rule
+    d = discretize(surf, 2)
+    if np.sum(np.einsum("ia,ia->i", d.xyz, d.nrm) * d.wts) < 0:
+        surf = build(True)
+    return surf
+
+
+def stellarator(p: int = 6, n_u: int = 24, n_v: int = 72):
+    """Stellarator surface with all on-surface nodes as targets (the points of the
+    paper's throughput table)."""
+    d = discretize(stellarator_surface(n_u, n_v), p)
+    return d, on_surface_targets(d)
+
+
 def flat_surface(tris: np.ndarray) -> Surface:
     """Planar triangles (k, 3, 3), mapped affinely."""
     tris = np.asarray(tris, dtype=np.float64)
