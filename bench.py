@@ -267,6 +267,7 @@ def bench_gpu(args):
                      "peak_note": "measured FP64 FMA peak (rrq_measure_fma_peak); FP32 FMA peak %.1f TFLOP/s" % peak32,
                      "flops_per_pair": fpp, "kernel_ms": pair_s * 1e3},
         "stage_ms": {"precompute": diag["ms_precompute"], "near_and_items": diag["ms_near"], "pairs": diag["ms_pairs"]},
+        "fit_kappa_max": diag["kappa_max"],
         "launch_shape": tuned,
         "clocks": clk,
         "gpu_launches": launches * args.steps if launches is not None else None,

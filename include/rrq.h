@@ -126,6 +126,10 @@ typedef struct {
     double ms_near, ms_precompute, ms_pairs;  /* stage times of the last build (ms) */
     int64_t kernel_launches; /* CUDA kernels the last build launched */
     double ms_apply_smooth, ms_apply_spmv;    /* kernel times of the last rrq_apply (ms) */
+    double kappa_max;        /* largest 1-norm condition number kappa_1(A) of a patch's fit
+                                matrix A (eq. dlpdensitylinearsystem2) in the last build, in
+                                the paper's harmonic normalisation (Sec. 5.1); INFINITY if a
+                                fit was singular */
 } rrq_diag;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
@@ -178,6 +182,16 @@ rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *t
  * NULL CSR gives it.  Synchronises the context stream; diagnostics as for a build. */
 rrq_status rrq_evaluate_near(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, uint32_t kernel_mask,
                              const double *density, double *out[4], const rrq_options *opt);
+
+/* Conditioning of the density fits (Sec. 5.1): for every patch P of `surf`, kappa[P] =
+ * kappa_1(A) = ||A||_1 ||A^{-1}||_1 of its quaternion harmonic system (eq.
+ * dlpdensitylinearsystem2, the 4 n_p x 4 n_p real block form) in the paper's
+ * normalisation of the harmonics (R_l^m of eq. rlmdef, H^{(l,m)} = sqrt2 Im S^{(l,m)}),
+ * on the patch scaled, translated and rotated as in Step 1; INFINITY where the fit is
+ * singular or the patch degenerate.  Runs the per-patch precompute only (no targets).
+ * With on_host != 0 the surface arrays and kappa ([npatch] doubles, caller-owned) are
+ * host memory, else device memory.  Synchronises the context stream. */
+rrq_status rrq_fit_condition(rrq_ctx *ctx, const rrq_surface *surf, double *kappa, int32_t on_host);
 
 /* Counters and stage timings of the last rrq_build_corrections on this context. */
 rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag);

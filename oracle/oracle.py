@@ -48,6 +48,7 @@ def lib():
             _lib.orc_surface_create.restype = C.c_void_p
             _lib.orc_surface_destroy.argtypes = [C.c_void_p]
             _lib.orc_T.restype = C.c_double
+            _lib.orc_patch_kappa.restype = C.c_double
             for name in ("orc_near", "orc_rows", "orc_patch_internals", "orc_edge_root",
                          "orc_pair_B", "orc_patch_bounds"):
                 getattr(_lib, name).restype = C.c_int
@@ -173,6 +174,10 @@ class OracleSurface:
             out[k] = out[k].reshape(4 * npn, npn)
         out["XS1"] = out["XS1"].reshape(npn, npn)
         return out
+
+    def patch_kappa(self, P: int) -> float:
+        """1-norm condition number of patch P's fit matrix A (Sec. 5.1)."""
+        return float(lib().orc_patch_kappa(C.c_void_p(self.h), C.c_int(P)))
 
     def pair_B(self, P: int, xt, nt, self_i: int = -1):
         p = int(self.order[P])

@@ -437,7 +437,7 @@ typedef struct {
     cplx *eg;                /* [3*pt][nh][3] grad S^{(j,k)} at edge samples */
     cplx *eh;                /* [3*pt][nh][3] (Hess S^{(j,k)}) tau at edge samples */
     double *XD, *XSp, *XS1, *XS2; /* fit matrices */
-    double kappa1;           /* (unused placeholder for diagnostics) */
+    double kappa1;           /* 1-norm condition number of the fit matrix A (Sec. 5.1) */
     int ok;
 } orc_patch;
 
@@ -629,8 +629,31 @@ static int patch_setup(orc_patch *P, const orc_order *O, const double *xyz, cons
             AEL(2, 0, i, j) = f2;  AEL(2, 1, i, j) = f3;  AEL(2, 3, i, j) = -f1;
             AEL(3, 0, i, j) = f3;  AEL(3, 1, i, j) = -f2; AEL(3, 2, i, j) = f1;
         }
+    /* ||A||_1 before factoring: largest column sum of |A| */
+    double anorm = 0;
+    for (int j = 0; j < n4; j++) {
+        double cs = 0;
+        for (int i = 0; i < n4; i++) cs += fabs(A[i * n4 + j]);
+        if (cs > anorm) anorm = cs;
+    }
     int *piv = malloc(sizeof(int) * n4);
     int bad = lu_factor(n4, A, piv);
+    /* kappa_1(A) = ||A||_1 ||A^{-1}||_1, the inverse from the LU factors */
+    P->kappa1 = INFINITY;
+    if (!bad) {
+        double *Ainv = malloc(sizeof(double) * n4 * n4);
+        memset(Ainv, 0, sizeof(double) * n4 * n4);
+        for (int i = 0; i < n4; i++) Ainv[i * n4 + i] = 1.0;
+        lu_solve(n4, A, piv, n4, Ainv);
+        double inorm = 0;
+        for (int j = 0; j < n4; j++) {
+            double cs = 0;
+            for (int i = 0; i < n4; i++) cs += fabs(Ainv[i * n4 + j]);
+            if (cs > inorm) inorm = cs;
+        }
+        P->kappa1 = anorm * inorm;
+        free(Ainv);
+    }
     P->XD = malloc(sizeof(double) * n4 * np);
     P->XSp = malloc(sizeof(double) * n4 * np);
     memset(P->XD, 0, sizeof(double) * n4 * np);
@@ -1359,6 +1382,20 @@ int orc_lu_solve(int n, const double *A, int nrhs, double *B) {
 
 /* Patch internals for tests: frame[13] = c, R (row-major), s; vertices[9];
  * y[np*3]; ea[3*p*3]; ey[3*pt*3]; et[3*pt*3]; XD, XSp [4np*np], XS1 [np*np], XS2 [4np*np]. */
+/* 1-norm condition number of patch P's fit matrix A (Sec. 5.1), or -1 on error */
+double orc_patch_kappa(void *h, int P) {
+    orc_surface *S = (orc_surface *)h;
+    if (!S || P < 0 || P >= S->npatch) return -1.0;
+    orc_patch pd;
+    if (setup_patch_of(S, P, &pd)) {
+        patch_free(&pd);
+        return -1.0;
+    }
+    const double k = pd.kappa1;
+    patch_free(&pd);
+    return k;
+}
+
 int orc_patch_internals(void *h, int P, double *frame, double *vert, double *y, double *ea,
                         double *ey, double *et, double *XD, double *XSp, double *XS1, double *XS2) {
     orc_surface *S = h;

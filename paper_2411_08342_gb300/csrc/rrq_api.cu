@@ -202,7 +202,37 @@ struct Prep {
     BuildCounters *d_cnt = nullptr;
     bool mixed = false;
     int newton_max = 30;
+    double kappa_max = 0;  // max over patches of kappa_1(A)
 };
+
+// Device arrays of the per-patch data (every array the precompute kernels write) in the
+// scratch arena; a failed allocation marks the arena failed.
+void alloc_patch_data(Scratch &s, size_t NPc, bool mixed, PatchData &pd) {
+    pd.frame = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_FRAME);
+    pd.bounds = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_BOUNDS);
+    pd.ynode = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
+    pd.xm = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
+    pd.ea = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ea());
+    pd.ey = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
+    pd.et = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
+    pd.eyu = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_eyu());
+    pd.eg = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
+    pd.eh = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
+    pd.eg2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
+    pd.eh2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
+    if (mixed) {
+        pd.XD2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
+        pd.XSp2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
+        pd.XS22 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
+        pd.XS12 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_XS1());
+    }
+    pd.XD = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
+    pd.XSp = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
+    pd.XS2 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
+    pd.XS1 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_XS1());
+    pd.status = (int *)Scratch::alloc(&s, sizeof(int) * NPc);
+    pd.kappa = (double *)Scratch::alloc(&s, sizeof(double) * NPc);
+}
 
 rrq_status build_prep(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const rrq_targets *targ, const rrq_options &o,
                       bool rowptr_for_caller, Prep &pr) {
@@ -235,29 +265,7 @@ rrq_status build_prep(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const r
     PatchData &pd = pr.pd;
     pd.npatch = in.npatch;
     pd.pmax = pmax;
-    pd.frame = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_FRAME);
-    pd.bounds = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_BOUNDS);
-    pd.ynode = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
-    pd.xm = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
-    pd.ea = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ea());
-    pd.ey = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
-    pd.et = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
-    pd.eyu = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_eyu());
-    pd.eg = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
-    pd.eh = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
-    pd.eg2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
-    pd.eh2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
-    if (mixed) {
-        pd.XD2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
-        pd.XSp2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
-        pd.XS22 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
-        pd.XS12 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_XS1());
-    }
-    pd.XD = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
-    pd.XSp = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
-    pd.XS2 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
-    pd.XS1 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_XS1());
-    pd.status = (int *)Scratch::alloc(&s, sizeof(int) * NPc);
+    alloc_patch_data(s, NPc, mixed, pd);
     std::vector<int32_t> rank(in.npatch);
     std::vector<int32_t> order_major;
     order_major.reserve(in.npatch);
@@ -301,9 +309,12 @@ rrq_status build_prep(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const r
     CK(cudaMemcpyAsync(&pr.nnz, pr.rowptr + in.ntarg, sizeof(int64_t), cudaMemcpyDeviceToHost, s.st));
     CK(cudaMemcpyAsync(pr.h_roff.data(), roff, sizeof(int64_t) * (in.npatch + 1), cudaMemcpyDeviceToHost, s.st));
     std::vector<int> h_status(in.npatch);
+    std::vector<double> h_kappa(in.npatch);
     CK(cudaMemcpyAsync(h_status.data(), pd.status, sizeof(int) * in.npatch, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(h_kappa.data(), pd.kappa, sizeof(double) * in.npatch, cudaMemcpyDeviceToHost, s.st));
     CK(cudaEventRecord(ctx->ev[2], s.st));
     CK(cudaStreamSynchronize(s.st));
+    pr.kappa_max = *std::max_element(h_kappa.begin(), h_kappa.end());
     for (int P = 0; P < in.npatch; P++)
         if (h_status[P]) return RRQ_ERR_DEGENERATE;
     return RRQ_OK;
@@ -419,6 +430,7 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     ctx->diag.ms_pairs = ms;
     ctx->diag.kernel_launches = rrq_launch_counter();
+    ctx->diag.kappa_max = pr.kappa_max;
     return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
 }
 
@@ -554,7 +566,43 @@ extern "C" rrq_status rrq_evaluate_near(rrq_ctx *ctx, const rrq_surface *surf, c
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     ctx->diag.ms_pairs = ms;
     ctx->diag.kernel_launches = rrq_launch_counter();
+    ctx->diag.kappa_max = pr.kappa_max;
     return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
+}
+
+extern "C" rrq_status rrq_fit_condition(rrq_ctx *ctx, const rrq_surface *surf, double *kappa, int32_t on_host) {
+    if (!ctx || !kappa) return RRQ_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    Scratch s;
+    s.st = ctx->stream;
+    Inputs in;
+    rrq_status rs = prepare_inputs(ctx, s, surf, nullptr, on_host != 0, false, in);
+    if (rs != RRQ_OK) return rs;
+    std::vector<std::vector<int32_t>> plist(RRQ_PMAX + 1);
+    std::vector<int32_t> order_major;
+    for (int P = 0; P < in.npatch; P++) plist[in.h_order[P]].push_back(P);
+    for (int p = 2; p <= RRQ_PMAX; p++)
+        if (!plist[p].empty()) {
+            rs = order_tables(ctx, p, surf->ref_uv[p], 0.0);
+            if (rs != RRQ_OK) return rs;
+            order_major.insert(order_major.end(), plist[p].begin(), plist[p].end());
+        }
+    PatchData pd{};
+    pd.npatch = in.npatch;
+    alloc_patch_data(s, in.npatch, false, pd);
+    int32_t *d_plists = (int32_t *)Scratch::alloc(&s, sizeof(int32_t) * in.npatch);
+    if (s.failed) return RRQ_ERR_OOM;
+    CK(cudaMemcpyAsync(d_plists, order_major.data(), sizeof(int32_t) * in.npatch, cudaMemcpyHostToDevice, s.st));
+    int start = 0;
+    for (int p = 2; p <= RRQ_PMAX; p++) {
+        const int n = (int)plist[p].size();
+        if (n) CK(rrq_launch_precompute(p, ctx->d_tab[p], d_plists + start, n, in.node_off, in.xyz, in.nrm, pd, s.st));
+        start += n;
+    }
+    CK(cudaMemcpyAsync(kappa, pd.kappa, sizeof(double) * in.npatch,
+                       on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    return RRQ_OK;
 }
 
 extern "C" rrq_status rrq_csr_copy(rrq_ctx *ctx, const rrq_csr *csr, int64_t *rowptr, int32_t *col, double *val[4],
@@ -1062,6 +1110,7 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     pd.XS2 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
     pd.XS1 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_XS1());
     pd.status = (int *)StaticArena::alloc(&ar, sizeof(int) * NPc);
+    pd.kappa = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc);
     int32_t *d_plists = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);
     int32_t *d_rank = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);
     BuildCounters *d_cnt = (BuildCounters *)StaticArena::alloc(&ar, sizeof(BuildCounters));
@@ -1105,8 +1154,11 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     std::vector<int> h_status(npatch);
     CK(cudaMemcpyAsync(&nnz, rowptr + ntarg, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h_roff.data(), roff, sizeof(int64_t) * (npatch + 1), cudaMemcpyDeviceToHost, st));
+    std::vector<double> h_kappa(npatch);
     CK(cudaMemcpyAsync(h_status.data(), pd.status, sizeof(int) * npatch, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_kappa.data(), pd.kappa, sizeof(double) * npatch, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    const double kappa_max = *std::max_element(h_kappa.begin(), h_kappa.end());
     if (nnz_out) *nnz_out = nnz;
     if (npairs_out) *npairs_out = nb.npairs;
     for (int P = 0; P < npatch; P++)
@@ -1153,5 +1205,6 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     ctx->diag.ssq_edges = (int64_t)hc.ssq_edges;
     ctx->diag.far_edges = (int64_t)hc.far_edges;
     ctx->diag.kernel_launches = rrq_launch_counter();
+    ctx->diag.kappa_max = kappa_max;
     return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
 }

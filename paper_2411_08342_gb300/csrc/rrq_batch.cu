@@ -6,6 +6,7 @@
 // CUDA graph and replayed by rrq_batch_execute.  The per-pair arithmetic is the same
 // as in rrq_build_corrections (same kernels); only the CSR columns are made local to
 // each surface (PatchData.col_off).
+#include <algorithm>
 #include <chrono>
 
 #include "rrq_host.h"
@@ -41,6 +42,7 @@ struct rrq_batch {
     int graph_kernels = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     double ms_create = 0, ms_autotune = 0, ms_last = 0;
+    double kappa_max = 0;  // max over all patches of kappa_1(A)
 
     void *alloc(size_t bytes) {
         void *p = nullptr;
@@ -249,13 +251,14 @@ rrq_status create_impl(rrq_ctx *ctx, rrq_batch *b, int32_t nsurf, const rrq_surf
     pd.XS2 = (double *)b->alloc(sizeof(double) * NP * pd_X());
     pd.XS1 = (double *)b->alloc(sizeof(double) * NP * pd_XS1());
     pd.status = (int *)b->alloc(sizeof(int) * NP);
+    pd.kappa = (double *)b->alloc(sizeof(double) * NP);
     pd.col_off = b->col_off;
     b->plists = (int32_t *)b->alloc(sizeof(int32_t) * NP);
     int32_t *d_rank = (int32_t *)Scratch::alloc(&s, sizeof(int32_t) * NP);
     b->cnt = (BuildCounters *)b->alloc(sizeof(BuildCounters));
     b->tile_ctr = (unsigned long long *)b->alloc(sizeof(unsigned long long) * (RRQ_PMAX + 1));
     if (!pd.frame || !pd.bounds || !pd.ynode || !pd.xm || !pd.ea || !pd.ey || !pd.et || !pd.eyu || !pd.eg || !pd.eh ||
-        (b->mixed && (!pd.eg2 || !pd.eh2)) || !pd.XD || !pd.XSp || !pd.XS2 || !pd.XS1 || !pd.status || !b->plists ||
+        (b->mixed && (!pd.eg2 || !pd.eh2)) || !pd.XD || !pd.XSp || !pd.XS2 || !pd.XS1 || !pd.status || !pd.kappa || !b->plists ||
         !d_rank || !b->cnt || !b->tile_ctr)
         return RRQ_ERR_OOM;
     CK(cudaMemcpyAsync(b->plists, order_major.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
@@ -266,8 +269,11 @@ rrq_status create_impl(rrq_ctx *ctx, rrq_batch *b, int32_t nsurf, const rrq_surf
             CK(rrq_launch_precompute(p, b->tab[p], b->plists + b->pl_start[p], b->pl_count[p], b->node_off, b->xyz,
                                      b->nrm, pd, st));
     std::vector<int> h_status(NP);
+    std::vector<double> h_kappa(NP);
     CK(cudaMemcpyAsync(h_status.data(), pd.status, sizeof(int) * NP, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_kappa.data(), pd.kappa, sizeof(double) * NP, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    b->kappa_max = *std::max_element(h_kappa.begin(), h_kappa.end());
     for (size_t P = 0; P < NP; P++)
         if (h_status[P]) return RRQ_ERR_DEGENERATE;
     // near list of every surface, merged into one list over the batch
@@ -438,6 +444,7 @@ extern "C" rrq_status rrq_batch_execute(rrq_ctx *ctx, rrq_batch *b) {
     ctx->diag.far_edges = (int64_t)hc.far_edges;
     ctx->diag.ms_pairs = ms;
     ctx->diag.kernel_launches = b->graph_kernels;
+    ctx->diag.kappa_max = b->kappa_max;
     return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
 }
 

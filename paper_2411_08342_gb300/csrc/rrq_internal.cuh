@@ -86,6 +86,7 @@ struct PatchData {
     double *XS1;     // [P][NPMAX][NPMAX]   scalar fit A_S^{-1}
     float2 *XD2, *XSp2, *XS22, *XS12;  // the four fit matrices as (hi, lo) float pairs, or NULL
     int *status;     // [P] 0 ok, nonzero = singular fit / degenerate patch
+    double *kappa;   // [P] 1-norm condition number of the fit matrix A (Sec. 5.1), or NULL
     double *xm;      // [P][NPMAX*3] monomial coefficients [ab][a] of the local node interpolant
     EdgeRoot *roots;  // [pair item][3 edges]: (Re t0, Im t0, converged, singularity swap)
     int8_t *uside;    // [pair item] side of the patch the target is on along e_z (+1, -1), 0 = unknown

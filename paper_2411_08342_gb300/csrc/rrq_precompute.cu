@@ -9,6 +9,8 @@
 //     quaternion modulus, for the right-hand sides (e_i, 0) [D] and (0, nu_i e_i) [S'];
 //     the scalar SLP system (eq. slpdensitylinearsystem) by LU with partial pivoting;
 //     and X_S2 = X_D Hn A_S^{-1} for the intermediate density of Thm. slpreduction.
+//   * when requested, kappa_1(A) of the quaternion system in the paper's normalisation
+//     (the conditioning study of Sec. 5.1).
 // One CTA per patch; everything lives in shared memory.
 #include <math.h>
 
@@ -53,6 +55,18 @@ __device__ __forceinline__ q4 qinv(const q4 &a) {
 
 // Table of Rn_n^q (unit-translation normalisation) for 0 <= q <= n <= L at the S
 // coordinates of y: S(x,y,z) = Rn(y,z,x).
+// d_lm = sqrt((l-m)! (l+m)!) for the lm-th fit harmonic (l = 1..p, m = 1..l, l-major):
+// the paper's R_l^m over the device's Rn_l^m.
+__device__ __forceinline__ double paper_norm(int lm) {
+    int l = 1;
+    while ((l + 1) * l / 2 <= lm) l++;
+    const int m = lm - l * (l - 1) / 2 + 1;
+    double f = 1.0;
+    for (int k = 2; k <= l - m; k++) f *= k;
+    for (int k = 2; k <= l + m; k++) f *= k;
+    return sqrt(f);
+}
+
 template <int L>
 __device__ void harmonic_table(const double *y, cd *S) {
     const double X = y[1], Y = y[2], Z = y[0];
@@ -330,6 +344,27 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         if (c >= NP && r == c - NP) { q[1] = snl[3 * r]; q[2] = snl[3 * r + 1]; q[3] = snl[3 * r + 2]; }
     }
     __syncthreads();
+    // Conditioning (Sec. 5.1): kappa_1(A) = ||A||_1 ||A^{-1}||_1 in the paper's normalisation
+    // R_l^m = d_lm Rn_l^m.  Every column (lm, component) of A holds the three components of
+    // d_lm grad H^{(l,m)} at the nodes, so ||A||_1 = max_lm d_lm sum_i (|F1| + |F2| + |F3|).
+    // TMP is free until the scalar fit is done.
+    __shared__ double s_anorm;
+    if (pd.kappa) {
+        for (int lm = tid; lm < NP; lm += nth) {
+            double s = 0;
+            for (int i = 0; i < NP; i++) {
+                const double *q = M + 4 * (i * NP + lm);
+                s += fabs(q[1]) + fabs(q[2]) + fabs(q[3]);
+            }
+            TMP[lm] = s * paper_norm(lm);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0;
+            for (int lm = 0; lm < NP; lm++) a = fmax(a, TMP[lm]);
+            s_anorm = a;
+        }
+    }
     // quaternion Gaussian elimination (left multiplication: sum_j M_rj c_j = W_r)
     __shared__ int s_piv;
     q4 *Mq = reinterpret_cast<q4 *>(M), *Wq = reinterpret_cast<q4 *>(W), *Lq = reinterpret_cast<q4 *>(sm + Z::LB_OFF);
@@ -379,6 +414,26 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         }
     }
     __syncthreads();
+    // ||A^{-1}||_1: column (i, 0) of A^{-1} is the fit of a unit density at node i, column
+    // (i, r) for r > 0 is that fit right-multiplied by a unit quaternion (the system is
+    // left-multiplication by quaternions), which only permutes and negates components.
+    // Coefficients in the paper's normalisation are the device ones divided by d_lm.
+    if (pd.kappa) {
+        for (int i = tid; i < NP; i += nth) {
+            double s = 0;
+            for (int lm = 0; lm < NP; lm++) {
+                const double *q = W + 4 * (lm * 2 * NP + i);
+                s += (fabs(q[0]) + fabs(q[1]) + fabs(q[2]) + fabs(q[3])) / paper_norm(lm);
+            }
+            TMP[NP + i] = s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0;
+            for (int i = 0; i < NP; i++) a = fmax(a, TMP[NP + i]);
+            pd.kappa[pid] = (s_bad || !(a == a)) ? INFINITY : s_anorm * a;
+        }
+    }
     // scalar fit: LU with partial pivoting on A_S, identity right-hand sides
     for (int k = 0; k < NP && !s_bad; k++) {
         if (tid == 0) {

@@ -46,7 +46,7 @@ class Diag(C.Structure):
     _fields_ = [("npairs", C.c_int64), ("newton_fail", C.c_int64), ("on_edge", C.c_int64), ("u_poor", C.c_int64),
                 ("ssq_edges", C.c_int64), ("far_edges", C.c_int64), ("ms_near", C.c_double),
                 ("ms_precompute", C.c_double), ("ms_pairs", C.c_double), ("kernel_launches", C.c_int64),
-                ("ms_apply_smooth", C.c_double), ("ms_apply_spmv", C.c_double)]
+                ("ms_apply_smooth", C.c_double), ("ms_apply_spmv", C.c_double), ("kappa_max", C.c_double)]
 
 
 class BatchInfo(C.Structure):
@@ -103,6 +103,7 @@ def load(build_if_needed: bool = True):
                                             C.c_void_p, C.c_void_p * 4, C.POINTER(Options)]
             L.rrq_autotune.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS), C.c_uint32,
                                        C.POINTER(Options)]
+            L.rrq_fit_condition.argtypes = [C.c_void_p, C.POINTER(Surface), C.c_void_p, C.c_int32]
             _lib = L
     return _lib
 
@@ -221,6 +222,19 @@ class Context:
         st = self.L.rrq_evaluate_near(self.h, C.byref(surf), C.byref(targ), mask, _ptr(density), arr, C.byref(opt))
         _check(st, "rrq_evaluate_near")
         return outs
+
+    def fit_condition(self, surf: Surface, on_host: bool = False):
+        """kappa_1(A) of every patch's fit system (rrq_fit_condition): a float64 CUDA tensor
+        [npatch], or a numpy array when the surface arrays are host memory."""
+        if on_host:
+            out = np.empty(surf.npatch)
+            ptr = out.ctypes.data
+        else:
+            import torch
+            out = torch.empty(surf.npatch, dtype=torch.float64, device=f"cuda:{self.device}")
+            ptr = out.data_ptr()
+        _check(self.L.rrq_fit_condition(self.h, C.byref(surf), ptr, int(on_host)), "rrq_fit_condition")
+        return out
 
     def autotune(self, surf: Surface, targ: TargetsS, kernels=("S", "D", "SP", "DP"), mixed: bool = False):
         """Measure the per-pair launch shapes on this problem and keep them in the context

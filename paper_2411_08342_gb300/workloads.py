@@ -305,6 +305,19 @@ def stellarator(p: int = 6, n_u: int = 24, n_v: int = 72):
     return d, on_surface_targets(d)
 
 
+def paraboloid_patch(H: float, h: float = 1.0) -> Surface:
+    """One patch of the paraboloid r(u, v) = (u, v, H (u^2 + v^2) / 2) over the equilateral
+    triangle of side h centred at the origin of the (u, v) plane (Sec. 5.1, eq. paraboloid);
+    its largest mean curvature, H, is reached at the origin."""
+    R = h / math.sqrt(3.0)
+    ang = 0.5 * math.pi + 2.0 * math.pi * np.arange(3) / 3.0
+    tri = np.stack([R * np.cos(ang), R * np.sin(ang), np.zeros(3)], -1)[None]
+
+    def lift(x):
+        return np.stack([x[..., 0], x[..., 1], 0.5 * H * (x[..., 0] ** 2 + x[..., 1] ** 2)], -1)
+    return Surface(f"paraboloid_H{H:g}_h{h:g}", 1, _flat_patch_map(tri, lift), {"H": H, "h": h})
+
+
 def flat_surface(tris: np.ndarray) -> Surface:
     """Planar triangles (k, 3, 3), mapped affinely."""
     tris = np.asarray(tris, dtype=np.float64)

@@ -11,6 +11,8 @@ import numpy as np
 import pytest
 from scipy.integrate import quad
 
+from paper_2411_08342_gb300 import workloads as W
+
 
 def test_addition_theorem(oracle_lib):
     """R_l^m(a+b) = sum_{j,k} R_j^k(a) R_{l-j}^{m-k}(b) T_{jk,lm} (Sec. 2.3, eqs.
@@ -151,3 +153,66 @@ def test_lu_solve(oracle_lib):
     A = rng.standard_normal((40, 40))
     B = rng.standard_normal((40, 3))
     assert np.abs(O.lu_solve(A, B) - np.linalg.solve(A, B)).max() < 1e-12
+
+
+def test_fit_condition_number(oracle_lib):
+    """kappa_1 of the fit matrix A of eq. dlpdensitylinearsystem2 (the oracle's, from its LU
+    inverse) equals numpy's 1-norm condition number of the same block matrix built here
+    from the harmonic gradients at the patch's local nodes, and grows with curvature and
+    order (Sec. 5.1)."""
+    O = oracle_lib
+    ks = {}
+    for p, lev in ((4, 1), (6, 1), (6, 3)):
+        d = W.discretize(W.star_surface(lev), p)
+        osf = O.OracleSurface(d)
+        info = osf.patch_internals(0)
+        y = info["y"]
+        npn = p * (p + 1) // 2
+        _, gH = O.basis_batch(p, y)
+        A = np.zeros((4 * npn, 4 * npn))
+        for i in range(npn):
+            for lm in range(npn):
+                f1, f2, f3 = gH[i, lm]
+                blk = [[0, -f1, -f2, -f3], [f1, 0, -f3, f2], [f2, f3, 0, -f1], [f3, -f2, f1, 0]]
+                for r in range(4):
+                    for c in range(4):
+                        A[r * npn + i, c * npn + lm] = blk[r][c]
+        k_np = np.linalg.cond(A, 1)
+        k_or = osf.patch_kappa(0)
+        assert abs(k_or - k_np) <= 1e-8 * k_np, (p, lev, k_or, k_np)
+        ks[(p, lev)] = k_or
+    assert ks[(6, 1)] > ks[(4, 1)]          # higher order on the same patch
+    assert ks[(6, 1)] > ks[(6, 3)]          # coarser (more curved) patch at the same order
+
+
+def _paraboloid_kappa(O, H, h, p, R=None, shift=None):
+    d = W.discretize(W.paraboloid_patch(H, h), p)
+    if R is not None:
+        d.xyz = d.xyz @ R.T + shift
+        d.nrm = d.nrm @ R.T
+    return O.OracleSurface(d).patch_kappa(0)
+
+
+def test_fit_condition_paraboloid(oracle_lib):
+    """kappa_1(A) on the paraboloid patch of eq. (paraboloid), against what Step 1 and
+    Sec. 5.1 fix:
+      * Step 1 scales the patch to unit longest side, so a patch of side h and curvature H
+        has the kappa of side 1 and curvature H h (exactly, up to rounding);
+      * Step 1 also removes rigid motions: a rotated and shifted patch has the same kappa;
+      * a small patch is nearly flat, so kappa(H, h) tends to the flat triangle's value as
+        h -> 0 (the right panel of the conditioning figure), decreasing on the way;
+      * on the flat triangle kappa grows with p (the left panel of the second figure)."""
+    O = oracle_lib
+    rot = np.array([[0.36, -0.48, 0.8], [0.8, 0.6, 0.0], [-0.48, 0.64, 0.6]])  # orthogonal
+    assert np.abs(rot @ rot.T - np.eye(3)).max() < 1e-15
+    flat = [_paraboloid_kappa(O, 0.0, 1.0, p) for p in range(2, 9)]
+    assert all(b > 3.0 * a for a, b in zip(flat, flat[1:])), flat
+    for p in (4, 6, 8):
+        k = _paraboloid_kappa(O, 10.0, 0.3, p)
+        assert abs(k / _paraboloid_kappa(O, 3.0, 1.0, p) - 1) < 1e-9, p
+        k_rot = _paraboloid_kappa(O, 3.0, 1.0, p, rot, np.array([1.0, -2.0, 0.5]))
+        assert abs(k_rot / _paraboloid_kappa(O, 3.0, 1.0, p) - 1) < 1e-9, p
+        seq = [_paraboloid_kappa(O, 10.0, 2.0 ** -L, p) for L in (2, 4, 6, 8, 10)]
+        assert all(b < a for a, b in zip(seq, seq[1:])), (p, seq)
+        assert abs(seq[-1] / flat[p - 2] - 1) < 0.03, (p, seq[-1], flat[p - 2])
+        assert _paraboloid_kappa(O, 10.0, 1.0, p) > 10 * flat[p - 2]
