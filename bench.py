@@ -241,7 +241,7 @@ def bench_gpu(args):
     # roofline of the dominant kernel (the per-pair kernel), FP64 ALU bound.  DRAM traffic of
     # k_pairs_tile<6, false, 4> on this workload from a one-pass ncu capture
     # (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
-    traffic = 3_269_866_240 + 3_975_148_544
+    traffic = None
     peak = ctx.fma_peak_tflops(fp32=False)
     peak32 = ctx.fma_peak_tflops(fp32=True)
     fpp = flops_per_pair(P)
@@ -262,7 +262,7 @@ def bench_gpu(args):
                    "l2": "512 MB flush between timed steps", "parallelism": f"weak x{world}"},
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "traffic_note": "bytes per launch of k_pairs_tile<6, false, 4>, one-pass ncu capture",
+                     "traffic": traffic, "traffic_note": "bytes per launch of k_pairs_tile<6, false, T>, one-pass ncu capture (null: kernel changed since the capture)",
                      "kernel": "k_roots<6> + k_uside<6> + k_pairs_tile<6, false, T> (one per-pair stage)",
                      "peak_note": "measured FP64 FMA peak (rrq_measure_fma_peak); FP32 FMA peak %.1f TFLOP/s" % peak32,
                      "flops_per_pair": fpp, "kernel_ms": pair_s * 1e3},
@@ -368,7 +368,7 @@ def evaluate_leg(ctx, surf, targ, d, tg, dev, ms_build: float, reps: int = 3) ->
 
 def stellarator_leg(ctx, dev) -> dict:
     """The stellarator of eq. stellarator (24 x 72 parameter cells, 3,456 patches, all nodes as
-    targets) at p = 4, 6, 8: points per second of an S-only and a D-only correction build
+    targets) at p = 4, 6, 8, 10, 12: points per second of an S-only and a D-only correction build
     (N / T with N the number of nodes, the measure of the paper's throughput table; one
     GB300 here, one CPU core there), and the relative max error of Green's identity
     1/2 u = S[du/dn] - D[u] for u = 1/|x| through rrq_apply."""
@@ -377,7 +377,7 @@ def stellarator_leg(ctx, dev) -> dict:
     from paper_2411_08342_gb300 import workloads as W
     stream = torch.cuda.current_stream(dev)
     out = {"workload": "stellarator 24x72 cells (3456 patches), on-surface nodes"}
-    for p in (4, 6, 8):
+    for p in (4, 6, 8, 10, 12):
         d, tg = W.stellarator(p)
         a = rrq.device_inputs(d, tg, device=str(dev))
         surf = ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv)
@@ -385,7 +385,7 @@ def stellarator_leg(ctx, dev) -> dict:
         row = {"points": d.nnode}
         for k in ("S", "D"):
             times = []
-            for it in range(3):
+            for it in range(3 if p <= 8 else 2):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 csr = ctx.build_corrections(surf, targ, (k,))
@@ -478,19 +478,24 @@ def e2e_leg(ctx, d, tg, nnz, dev, flush, args, world, total_entries):
     out_vals = {k: torch.empty(nnz, dtype=torch.float64).pin_memory().numpy() for k in KERNELS}
     h2d = sum(v.nbytes for v in pin.values())
     d2h = out_rowptr.nbytes + out_col.nbytes + sum(v.nbytes for v in out_vals.values())
-    times = []
+    times, parts = [], []
     for it in range(max(2, args.steps // 2) + 1):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        csr = ctx.build_corrections(hsurf, htarg, KERNELS, inputs_on_host=True)
+        csr = ctx.build_corrections(hsurf, htarg, KERNELS, inputs_on_host=True)   # returns after the build
+        t1 = time.perf_counter()
         ctx.csr_to_host(csr, KERNELS, out=(out_rowptr, out_col, out_vals))
+        t2 = time.perf_counter()
         ctx.csr_free(csr)
         torch.cuda.synchronize(dev)
         if it > 0:
             times.append(time.perf_counter() - t0)
+            parts.append((t1 - t0, t2 - t1))
     e2e_s = reduce_max(sum(times) / len(times), world, dev)
-    return {"value": total_entries / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return {"value": total_entries / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_build_host_inputs": 1e3 * sum(p[0] for p in parts) / len(parts),
+            "ms_copy_to_host": 1e3 * sum(p[1] for p in parts) / len(parts)}
 
 
 def cpu_baseline(ntarg_sample: int) -> dict:

@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define RRQ_PMAX 8
+#define RRQ_PMAX 12
 
 typedef int32_t rrq_status;
 enum {

@@ -236,6 +236,14 @@ def ssq_moments(n: int, a: float, b: float):
     return J, K
 
 
+def ssq_weights(pt: int, a: float, b: float):
+    """Singularity-swap weights (m = 1, 3) at the pt Gauss-Legendre nodes for t0 = a + i b."""
+    l1, l3 = np.zeros(pt), np.zeros(pt)
+    if lib().orc_ssq_weights(C.c_int(pt), C.c_double(a), C.c_double(b), _p(l1), _p(l3)):
+        raise ValueError("bad arguments")
+    return l1, l3
+
+
 def bernstein_rho(z: complex) -> float:
     r = C.c_double()
     lib().orc_bernstein_rho(C.c_double(z.real), C.c_double(z.imag), C.byref(r))

@@ -324,11 +324,19 @@ static void dubiner(int deg, double u, double v, double *out) {
 /* Per-order tables                                                           */
 /* ------------------------------------------------------------------------- */
 
+/* LU factors (with pivots) of V^T, V[q][i] = t_q^i, for the edge nodes t_q (Sec. 3.4). */
+static int vt_factor(int pt, const double *tq, double *lu, int *piv) {
+    for (int i = 0; i < pt; i++)
+        for (int q = 0; q < pt; q++) lu[i * pt + q] = pow(tq[q], i);
+    return lu_factor(pt, lu, piv);
+}
+
 typedef struct {
     int p, np, pt, nup;
     double rho0;
     double tq[ORC_PTMAX], wq[ORC_PTMAX];          /* edge GL nodes */
-    double U[ORC_PTMAX * ORC_PTMAX];              /* c~ = U F (inverse Vandermonde) */
+    double VtLU[ORC_PTMAX * ORC_PTMAX];           /* LU factors of V^T, V[q][i] = t_q^i (Sec. 3.4) */
+    int Vtpiv[ORC_PTMAX];                         /* its pivots */
     double tu[2 * ORC_PTMAX], wu[2 * ORC_PTMAX];  /* upsampled GL */
     double Lup[2 * ORC_PTMAX * ORC_PTMAX];        /* Lagrange of edge nodes at tu */
     double tom[ORC_NOM], wom[ORC_NOM];            /* GL per Omega_0 panel */
@@ -358,16 +366,12 @@ static int order_init(orc_order *O, int p, const double *ref_uv, const orc_opts 
     gauss_legendre(pt, O->tq, O->wq);
     gauss_legendre(O->nup, O->tu, O->wu);
     gauss_legendre(ORC_NOM, O->tom, O->wom);
-    /* U = inverse of the monomial Vandermonde [t_q^i] (Sec. 3.4) */
-    double *V = malloc(sizeof(double) * pt * pt);
-    int piv[ORC_PTMAX];
-    for (int q = 0; q < pt; q++)
-        for (int i = 0; i < pt; i++) V[q * pt + i] = pow(O->tq[q], i);
-    for (int i = 0; i < pt * pt; i++) O->U[i] = 0.0;
-    for (int i = 0; i < pt; i++) O->U[i * pt + i] = 1.0;
-    if (lu_factor(pt, V, piv)) { free(V); return -1; }
-    lu_solve(pt, V, piv, pt, O->U);
-    free(V);
+    /* Sec. 3.4 writes c~ = U F with U the inverse of the monomial Vandermonde V[q][i] = t_q^i;
+     * then I = sum_i c~_i I_i = lambda . F with V^T lambda = (I_0 .. I_{pt-1}).  Following
+     * Sec. 5.1 (the conditioning of V is harmless when the system is solved by a backward
+     * stable method), lambda is obtained by solving that system with the LU factors of V^T,
+     * not by multiplying with an explicitly formed inverse, whose product cancels. */
+    if (vt_factor(pt, O->tq, O->VtLU, O->Vtpiv)) return -1;
     /* Lagrange basis of the pt edge nodes at the upsampled nodes */
     for (int s = 0; s < O->nup; s++)
         for (int q = 0; q < pt; q++) {
@@ -772,12 +776,11 @@ static void edge_weights(const orc_order *O, const double *ea, int p, const doub
         double a = creal(t0), b = cimag(t0);
         double J[ORC_PTMAX], K[ORC_PTMAX];
         ssq_moments(pt, a, b, J, want3 ? K : NULL);
+        /* lambda = V^{-T} I for m = 1 and 3 */
+        lu_solve(pt, O->VtLU, O->Vtpiv, 1, J);
+        if (want3) lu_solve(pt, O->VtLU, O->Vtpiv, 1, K);
         for (int q = 0; q < pt; q++) {
-            double l1 = 0, l3 = 0;
-            for (int i = 0; i < pt; i++) {
-                l1 += O->U[i * pt + q] * J[i];
-                if (want3) l3 += O->U[i * pt + q] * K[i];
-            }
+            const double l1 = J[q], l3 = want3 ? K[q] : 0.0;
             double d[3] = {yt[0] - eyq[3 * q], yt[1] - eyq[3 * q + 1], yt[2] - eyq[3 * q + 2]};
             double rq = sqrt(dot3(d, d));
             double ratio = cabs(O->tq[q] - t0) / rq;
@@ -1367,6 +1370,21 @@ double orc_T(int j, int k, int l, int m) { binom_init(); return Tcoef(j, k, l, m
 int orc_gauss_legendre(int n, double *x, double *w) { gauss_legendre(n, x, w); return 0; }
 
 int orc_ssq_moments(int n, double a, double b, double *J, double *K) { ssq_moments(n, a, b, J, K); return 0; }
+
+/* Singularity-swap weights on [-1, 1] for the pt Gauss-Legendre nodes: l1[q], l3[q] with
+ * int f(t) / ((t - a)^2 + b^2)^{m/2} dt = sum_q l_m[q] f(t_q) for polynomials f of degree
+ * < pt (m = 1, 3), lambda = V^{-T} I as in the edge rule. */
+int orc_ssq_weights(int pt, double a, double b, double *l1, double *l3) {
+    if (pt < 1 || pt > ORC_PTMAX) return -1;
+    double tq[ORC_PTMAX], wq[ORC_PTMAX], lu[ORC_PTMAX * ORC_PTMAX];
+    int piv[ORC_PTMAX];
+    gauss_legendre(pt, tq, wq);
+    if (vt_factor(pt, tq, lu, piv)) return -1;
+    ssq_moments(pt, a, b, l1, l3);
+    lu_solve(pt, lu, piv, 1, l1);
+    lu_solve(pt, lu, piv, 1, l3);
+    return 0;
+}
 
 int orc_bernstein_rho(double re, double im, double *rho) { *rho = bernstein_rho(re + I * im); return 0; }
 

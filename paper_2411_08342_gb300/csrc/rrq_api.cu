@@ -29,6 +29,10 @@ RRQ_DECL_PAIRS(5)
 RRQ_DECL_PAIRS(6)
 RRQ_DECL_PAIRS(7)
 RRQ_DECL_PAIRS(8)
+RRQ_DECL_PAIRS(9)
+RRQ_DECL_PAIRS(10)
+RRQ_DECL_PAIRS(11)
+RRQ_DECL_PAIRS(12)
 #undef RRQ_DECL_PAIRS
 
 cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape shape, cudaStream_t st) {
@@ -36,6 +40,7 @@ cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape sha
 #define RRQ_CASE(P) \
     case P: return rrq_launch_pairs_p##P(mixed, a, shape, st);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
+        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12)
 #undef RRQ_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -46,6 +51,7 @@ cudaError_t rrq_launch_pairs_eval(int p, const PairArgs &a, PairShape shape, cud
 #define RRQ_CASE(P) \
     case P: return rrq_launch_pairs_eval_p##P(a, shape, st);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
+        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12)
 #undef RRQ_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -56,6 +62,7 @@ int rrq_pair_tiles(int p, int tiles[4]) {
 #define RRQ_CASE(P) \
     case P: return rrq_pair_tiles_p##P(tiles);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
+        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12)
 #undef RRQ_CASE
         default: return 0;
     }
@@ -210,26 +217,26 @@ struct Prep {
 void alloc_patch_data(Scratch &s, size_t NPc, bool mixed, PatchData &pd) {
     pd.frame = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_FRAME);
     pd.bounds = (double *)Scratch::alloc(&s, sizeof(double) * NPc * PD_BOUNDS);
-    pd.ynode = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
-    pd.xm = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode());
-    pd.ea = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ea());
-    pd.ey = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
-    pd.et = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey());
-    pd.eyu = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_eyu());
-    pd.eg = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
-    pd.eh = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg());
-    pd.eg2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
-    pd.eh2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg()) : nullptr;
+    pd.ynode = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode(pd.pmax));
+    pd.xm = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ynode(pd.pmax));
+    pd.ea = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ea(pd.pmax));
+    pd.ey = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey(pd.pmax));
+    pd.et = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_ey(pd.pmax));
+    pd.eyu = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_eyu(pd.pmax));
+    pd.eg = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg(pd.pmax));
+    pd.eh = (cd *)Scratch::alloc(&s, sizeof(cd) * NPc * pd_eg(pd.pmax));
+    pd.eg2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg(pd.pmax)) : nullptr;
+    pd.eh2 = mixed ? (float4 *)Scratch::alloc(&s, sizeof(float4) * NPc * pd_eg(pd.pmax)) : nullptr;
     if (mixed) {
-        pd.XD2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
-        pd.XSp2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
-        pd.XS22 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X());
-        pd.XS12 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_XS1());
+        pd.XD2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X(pd.pmax));
+        pd.XSp2 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X(pd.pmax));
+        pd.XS22 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_X(pd.pmax));
+        pd.XS12 = (float2 *)Scratch::alloc(&s, sizeof(float2) * NPc * pd_XS1(pd.pmax));
     }
-    pd.XD = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
-    pd.XSp = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
-    pd.XS2 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X());
-    pd.XS1 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_XS1());
+    pd.XD = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X(pd.pmax));
+    pd.XSp = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X(pd.pmax));
+    pd.XS2 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_X(pd.pmax));
+    pd.XS1 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_XS1(pd.pmax));
     pd.status = (int *)Scratch::alloc(&s, sizeof(int) * NPc);
     pd.kappa = (double *)Scratch::alloc(&s, sizeof(double) * NPc);
 }
@@ -458,11 +465,11 @@ __global__ void k_patch_coef(const int32_t *__restrict__ order, const int64_t *_
         if (r < 12 * np) {
             const int blk = r / (4 * np);
             row = r % (4 * np);
-            X = (blk == 0 ? pd.XD : blk == 1 ? pd.XSp : pd.XS2) + (size_t)P * pd_X();
+            X = (blk == 0 ? pd.XD : blk == 1 ? pd.XSp : pd.XS2) + (size_t)P * pd_X(pd.pmax);
             dst = c + blk * 4 * RRQ_NPMAX;
         } else {
             row = r - 12 * np;
-            X = pd.XS1 + (size_t)P * pd_XS1();
+            X = pd.XS1 + (size_t)P * pd_XS1(pd.pmax);
             dst = c + 12 * RRQ_NPMAX;
         }
         double v = 0.0;
@@ -589,6 +596,8 @@ extern "C" rrq_status rrq_fit_condition(rrq_ctx *ctx, const rrq_surface *surf, d
         }
     PatchData pd{};
     pd.npatch = in.npatch;
+    for (int p = 2; p <= RRQ_PMAX; p++)
+        if (!plist[p].empty()) pd.pmax = p;
     alloc_patch_data(s, in.npatch, false, pd);
     int32_t *d_plists = (int32_t *)Scratch::alloc(&s, sizeof(int32_t) * in.npatch);
     if (s.failed) return RRQ_ERR_OOM;
@@ -1095,20 +1104,20 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     pd.pmax = pmax;
     pd.frame = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * PD_FRAME);
     pd.bounds = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * PD_BOUNDS);
-    pd.ynode = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ynode());
-    pd.xm = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ynode());
-    pd.ea = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ea());
-    pd.ey = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey());
-    pd.et = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey());
-    pd.eyu = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_eyu());
-    pd.eg = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg());
-    pd.eh = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg());
+    pd.ynode = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ynode(pd.pmax));
+    pd.xm = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ynode(pd.pmax));
+    pd.ea = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ea(pd.pmax));
+    pd.ey = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey(pd.pmax));
+    pd.et = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_ey(pd.pmax));
+    pd.eyu = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_eyu(pd.pmax));
+    pd.eg = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg(pd.pmax));
+    pd.eh = (cd *)StaticArena::alloc(&ar, sizeof(cd) * NPc * pd_eg(pd.pmax));
     pd.eg2 = nullptr;
     pd.eh2 = nullptr;
-    pd.XD = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
-    pd.XSp = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
-    pd.XS2 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X());
-    pd.XS1 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_XS1());
+    pd.XD = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X(pd.pmax));
+    pd.XSp = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X(pd.pmax));
+    pd.XS2 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X(pd.pmax));
+    pd.XS1 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_XS1(pd.pmax));
     pd.status = (int *)StaticArena::alloc(&ar, sizeof(int) * NPc);
     pd.kappa = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc);
     int32_t *d_plists = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);

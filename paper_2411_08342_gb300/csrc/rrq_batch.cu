@@ -229,27 +229,27 @@ rrq_status create_impl(rrq_ctx *ctx, rrq_batch *b, int32_t nsurf, const rrq_surf
     for (size_t r = 0; r < NP; r++) rank[order_major[r]] = (int32_t)r;
     pd.frame = (double *)b->alloc(sizeof(double) * NP * PD_FRAME);
     pd.bounds = (double *)b->alloc(sizeof(double) * NP * PD_BOUNDS);
-    pd.ynode = (double *)b->alloc(sizeof(double) * NP * pd_ynode());
-    pd.xm = (double *)b->alloc(sizeof(double) * NP * pd_ynode());
-    pd.ea = (double *)b->alloc(sizeof(double) * NP * pd_ea());
-    pd.ey = (double *)b->alloc(sizeof(double) * NP * pd_ey());
-    pd.et = (double *)b->alloc(sizeof(double) * NP * pd_ey());
-    pd.eyu = (double *)b->alloc(sizeof(double) * NP * pd_eyu());
-    pd.eg = (cd *)b->alloc(sizeof(cd) * NP * pd_eg());
-    pd.eh = (cd *)b->alloc(sizeof(cd) * NP * pd_eg());
-    pd.eg2 = b->mixed ? (float4 *)b->alloc(sizeof(float4) * NP * pd_eg()) : nullptr;
-    pd.eh2 = b->mixed ? (float4 *)b->alloc(sizeof(float4) * NP * pd_eg()) : nullptr;
+    pd.ynode = (double *)b->alloc(sizeof(double) * NP * pd_ynode(pd.pmax));
+    pd.xm = (double *)b->alloc(sizeof(double) * NP * pd_ynode(pd.pmax));
+    pd.ea = (double *)b->alloc(sizeof(double) * NP * pd_ea(pd.pmax));
+    pd.ey = (double *)b->alloc(sizeof(double) * NP * pd_ey(pd.pmax));
+    pd.et = (double *)b->alloc(sizeof(double) * NP * pd_ey(pd.pmax));
+    pd.eyu = (double *)b->alloc(sizeof(double) * NP * pd_eyu(pd.pmax));
+    pd.eg = (cd *)b->alloc(sizeof(cd) * NP * pd_eg(pd.pmax));
+    pd.eh = (cd *)b->alloc(sizeof(cd) * NP * pd_eg(pd.pmax));
+    pd.eg2 = b->mixed ? (float4 *)b->alloc(sizeof(float4) * NP * pd_eg(pd.pmax)) : nullptr;
+    pd.eh2 = b->mixed ? (float4 *)b->alloc(sizeof(float4) * NP * pd_eg(pd.pmax)) : nullptr;
     if (b->mixed) {
-        pd.XD2 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X());
-        pd.XSp2 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X());
-        pd.XS22 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X());
-        pd.XS12 = (float2 *)b->alloc(sizeof(float2) * NP * pd_XS1());
+        pd.XD2 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X(pd.pmax));
+        pd.XSp2 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X(pd.pmax));
+        pd.XS22 = (float2 *)b->alloc(sizeof(float2) * NP * pd_X(pd.pmax));
+        pd.XS12 = (float2 *)b->alloc(sizeof(float2) * NP * pd_XS1(pd.pmax));
         if (!pd.XD2 || !pd.XSp2 || !pd.XS22 || !pd.XS12) return RRQ_ERR_OOM;
     }
-    pd.XD = (double *)b->alloc(sizeof(double) * NP * pd_X());
-    pd.XSp = (double *)b->alloc(sizeof(double) * NP * pd_X());
-    pd.XS2 = (double *)b->alloc(sizeof(double) * NP * pd_X());
-    pd.XS1 = (double *)b->alloc(sizeof(double) * NP * pd_XS1());
+    pd.XD = (double *)b->alloc(sizeof(double) * NP * pd_X(pd.pmax));
+    pd.XSp = (double *)b->alloc(sizeof(double) * NP * pd_X(pd.pmax));
+    pd.XS2 = (double *)b->alloc(sizeof(double) * NP * pd_X(pd.pmax));
+    pd.XS1 = (double *)b->alloc(sizeof(double) * NP * pd_XS1(pd.pmax));
     pd.status = (int *)b->alloc(sizeof(int) * NP);
     pd.kappa = (double *)b->alloc(sizeof(double) * NP);
     pd.col_off = b->col_off;

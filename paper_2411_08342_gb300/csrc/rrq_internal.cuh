@@ -47,7 +47,7 @@ struct OrderTables {
     int p, np, pt, nup, njk;
     double rho0;
     double tq[RRQ_PTMAX], wq[RRQ_PTMAX];            // edge Gauss-Legendre nodes/weights
-    double U[RRQ_PTMAX * RRQ_PTMAX];                // [i][q]: monomial coefficients c_i = sum_q U[i][q] F_q
+    double BPr[RRQ_PTMAX * RRQ_PTMAX];              // [k][i] 1/(tq[i] - tq[i-k-1]), i > k: dual Vandermonde solve
     double tu[2 * RRQ_PTMAX], wu[2 * RRQ_PTMAX];    // upsampled Gauss-Legendre rule
     double Lup[2 * RRQ_PTMAX * RRQ_PTMAX];          // [s][q] Lagrange basis of tq at tu[s]
     double tom[RRQ_NOM], wom[RRQ_NOM];              // Gauss-Legendre rule per Omega_0 panel
@@ -65,7 +65,8 @@ struct EdgeRoot {
     double x, y, z, w;
 };
 
-// Device-side per-patch data (strides sized for the largest order of the surface).
+// Device-side per-patch data; per-patch strides are those of the largest order pmax of the
+// build (pd_*(pmax) below), the layout inside a patch is that of the patch's own order.
 struct PatchData {
     int npatch;
     int pmax;
@@ -94,13 +95,15 @@ struct PatchData {
 };
 
 static const size_t PD_FRAME = 16, PD_BOUNDS = 5;
-__host__ __device__ __forceinline__ size_t pd_ynode() { return (size_t)RRQ_NPMAX * 3; }
-__host__ __device__ __forceinline__ size_t pd_ea() { return (size_t)3 * RRQ_PMAX * 3; }
-__host__ __device__ __forceinline__ size_t pd_ey() { return (size_t)3 * RRQ_PTMAX * 3; }
-__host__ __device__ __forceinline__ size_t pd_eyu() { return (size_t)3 * 2 * RRQ_PTMAX * 3; }
-__host__ __device__ __forceinline__ size_t pd_eg() { return (size_t)3 * RRQ_PTMAX * RRQ_NJKMAX * 3; }
-__host__ __device__ __forceinline__ size_t pd_X() { return (size_t)4 * RRQ_NPMAX * RRQ_NPMAX; }
-__host__ __device__ __forceinline__ size_t pd_XS1() { return (size_t)RRQ_NPMAX * RRQ_NPMAX; }
+// Per-patch strides of the PatchData arrays, for the largest order pm of the build.
+__host__ __device__ __forceinline__ size_t pd_np(int pm) { return (size_t)pm * (pm + 1) / 2; }
+__host__ __device__ __forceinline__ size_t pd_ynode(int pm) { return pd_np(pm) * 3; }
+__host__ __device__ __forceinline__ size_t pd_ea(int pm) { return (size_t)3 * pm * 3; }
+__host__ __device__ __forceinline__ size_t pd_ey(int pm) { return (size_t)3 * 2 * pm * 3; }
+__host__ __device__ __forceinline__ size_t pd_eyu(int pm) { return (size_t)3 * 4 * pm * 3; }
+__host__ __device__ __forceinline__ size_t pd_eg(int pm) { return (size_t)3 * 2 * pm * ((pm + 1) * (pm + 2) / 2) * 3; }
+__host__ __device__ __forceinline__ size_t pd_X(int pm) { return 4 * pd_np(pm) * pd_np(pm); }
+__host__ __device__ __forceinline__ size_t pd_XS1(int pm) { return pd_np(pm) * pd_np(pm); }
 
 // Pair work item: target, patch, offset of the first CSR entry of the pair, and the
 // pair's index in target-major order (near-list order).

@@ -77,10 +77,53 @@ __device__ __forceinline__ cd sqrt_c(cd z) {
 
 // 1/n for n = 0 .. 2 RRQ_PMAX + 1 (entry 0 unused)
 __device__ __forceinline__ double rcp_small(int n) {
-    constexpr double R[2 * RRQ_PMAX + 2] = {0.0,       1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,
-                                            1.0 / 6,   1.0 / 7,    1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11,
-                                            1.0 / 12,  1.0 / 13,   1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17};
+    constexpr double R[2 * RRQ_PMAX + 2] = {0.0,      1.0,      1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
+                                            1.0 / 7,  1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13,
+                                            1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20,
+                                            1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25};
     return R[n];
+}
+
+// Singularity-swap weights from the moments: solves V^T lam = mom in place, V[q][i] = x_q^i
+// (x the PT edge nodes), so that sum_q lam_q F(x_q) = sum_i c_i mom_i for the monomial
+// coefficients c of the interpolant of F (Sec. 3.4).  The dual algorithm of Bjorck and
+// Pereyra (Math. Comp. 24, 1970): Newton-form differences, then back to the power basis,
+// with the reciprocal node differences rd[k][i] = 1/(x_i - x_{i-k-1}) tabulated.  It is
+// accurate to rounding for Gauss-Legendre nodes even where cond(V) ~ 1e10 (PT = 24),
+// whereas a product with an explicitly formed inverse cancels.
+template <int PT>
+__device__ __forceinline__ void dual_vandermonde_solve(double *mom, const double *x, const double *rd) {
+    if constexpr (PT <= 12) {
+        // in registers, fully unrolled
+        double a[PT];
+#pragma unroll
+        for (int i = 0; i < PT; i++) a[i] = mom[i];
+#pragma unroll
+        for (int k = 0; k < PT - 1; k++) {
+            const double xk = x[k];
+#pragma unroll
+            for (int i = PT - 1; i > k; i--) a[i] = fma(-xk, a[i - 1], a[i]);
+        }
+#pragma unroll
+        for (int k = PT - 2; k >= 0; k--) {
+#pragma unroll
+            for (int i = k + 1; i < PT; i++) a[i] *= rd[k * PT + i];
+#pragma unroll
+            for (int i = k; i < PT - 1; i++) a[i] -= a[i + 1];
+        }
+#pragma unroll
+        for (int i = 0; i < PT; i++) mom[i] = a[i];
+    } else {
+        // higher orders: in place (shared memory), the same steps
+        for (int k = 0; k < PT - 1; k++) {
+            const double xk = x[k];
+            for (int i = PT - 1; i > k; i--) mom[i] = fma(-xk, mom[i - 1], mom[i]);
+        }
+        for (int k = PT - 2; k >= 0; k--) {
+            for (int i = k + 1; i < PT; i++) mom[i] *= rd[k * PT + i];
+            for (int i = k; i < PT - 1; i++) mom[i] -= mom[i + 1];
+        }
+    }
 }
 
 // Table of Rn_n^q (0 <= q <= n <= P), column m = lane computed by the warp.

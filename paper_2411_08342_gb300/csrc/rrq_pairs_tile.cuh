@@ -132,7 +132,11 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
     const double inv4pi = 0.07957747154594767, sq2 = 1.4142135623730951;
     constexpr double FACT[2 * RRQ_PMAX + 2] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0, 5040.0, 40320.0, 362880.0,
                                                3628800.0, 39916800.0, 479001600.0, 6227020800.0, 87178291200.0,
-                                               1307674368000.0, 20922789888000.0, 355687428096000.0};
+                                               1307674368000.0, 20922789888000.0, 355687428096000.0,
+                                               6402373705728000.0, 121645100408832000.0, 2432902008176640000.0,
+                                               51090942171709440000.0, 1124000727777607680000.0,
+                                               25852016738884976640000.0, 620448401733239439360000.0,
+                                               15511210043330985984000000.0};
 #define SW(pl) (smraw + (size_t)(pl) * Z::TOTAL)
     // tiles of T consecutive items: grid-stride, or (persistent launch) fetched from a counter
     for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             if (it < 13) sw[Z::FR + it] = pd.frame[(size_t)im.P * PD_FRAME + it];
             else if (it < 16) sw[Z::XT + it - 13] = txyz[3 * im.t + it - 13];
             else if (it < 19) sw[Z::NT + it - 16] = tnrm[3 * im.t + it - 16];
-            else sw[Z::EA + it - 19] = pd.ea[(size_t)im.P * pd_ea() + it - 19];
+            else sw[Z::EA + it - 19] = pd.ea[(size_t)im.P * pd_ea(pd.pmax) + it - 19];
         }
         __syncthreads();
         // B: target in the patch frame; self index
@@ -189,8 +193,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const double *yt = sw + Z::YT;
             if (it < NS) {
                 const int q = it;
-                const double *ey = pd.ey + ps * pd_ey() + 3 * q;
-                const double *et = pd.et + ps * pd_ey() + 3 * q;
+                const double *ey = pd.ey + ps * pd_ey(pd.pmax) + 3 * q;
+                const double *et = pd.et + ps * pd_ey(pd.pmax) + 3 * q;
                 const double d0 = yt[0] - ey[0], d1 = yt[1] - ey[1], d2 = yt[2] - ey[2];
                 double *dq = sw + Z::DQ, *tau = sw + Z::TAU;
                 dq[3 * q] = d0; dq[3 * q + 1] = d1; dq[3 * q + 2] = d2;
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             for (int s2 = lane; s2 < NP + NS; s2 += 32) {
                 double dz, dl2;
                 if (s2 < NP) {
-                    const double *yn = pd.ynode + ps * pd_ynode() + 3 * s2;
+                    const double *yn = pd.ynode + ps * pd_ynode(pd.pmax) + 3 * s2;
                     const double d0 = yt[0] - yn[0], d1 = yt[1] - yn[1];
                     dz = yt[2] - yn[2];
                     dl2 = d0 * d0 + d1 * d1 + dz * dz;
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 if ((uz > 0 ? mplus : mminus) < -0.5) atomicAdd(&bc[2], 1u);
             }
         }
-        // F: complex roots (from k_roots) and singularity-swap moments, one thread per (pair, edge)
+        // F: complex roots (from k_roots), singularity-swap moments and weights, one thread per (pair, edge)
         for (int f = tid; f < nt * 3; f += nth) {
             const int pl = f / 3, e = f % 3;
             double *sw = SW(pl);
@@ -305,7 +309,9 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     K[0] = ((1 - a) / sp + (1 + a) / sm) / (bi * bi);
                     K[1] = (1.0 / sm - 1.0 / sp) + a * K[0];
                     for (int i = 0; i + 2 < PT; i++) K[i + 2] = J[i] + 2.0 * a * K[i + 1] - c0 * K[i];
+                    dual_vandermonde_solve<PT>(K, tab->tq, tab->BPr);   // K uses J: solve J after it
                 }
+                dual_vandermonde_solve<PT>(J, tab->tq, tab->BPr);      // moments -> weights lambda
             }
         }
         __syncthreads();
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             double *sw = SW(pl);
             if (sw[Z::T0 + 4 * e + 3] != 0.0) continue;
             const double *yt = sw + Z::YT;
-            const double *yu = pd.eyu + (size_t)s_item[pl].P * pd_eyu() + 3 * (e * NUP + s2);
+            const double *yu = pd.eyu + (size_t)s_item[pl].P * pd_eyu(pd.pmax) + 3 * (e * NUP + s2);
             const double d0 = yt[0] - yu[0], d1 = yt[1] - yu[1], d2 = yt[2] - yu[2];
             const double r2 = d0 * d0 + d1 * d1 + d2 * d2, r = sqrt(r2);
             const double k1 = tab->wu[s2] / r;
@@ -331,13 +337,9 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const double *t0s = sw + Z::T0;
             double w1, w3;
             if (t0s[4 * e + 3] != 0.0) {
+                // lambda (phase F) for m = 1 and m = 3
                 const double *J = sw + Z::MOM + 2 * NUP * e, *K = J + PT;
-                double l1 = 0, l3 = 0;
-                for (int i = 0; i < PT; i++) {
-                    const double u = tab->U[i * PT + q];
-                    l1 = fma(u, J[i], l1);
-                    if (wantDP) l3 = fma(u, K[i], l3);
-                }
+                const double l1 = J[q], l3 = wantDP ? K[q] : 0.0;
                 const double dtr = tab->tq[q] - t0s[4 * e], ti = t0s[4 * e + 1];
                 const double ratio = sqrt(dtr * dtr + ti * ti) * sw[Z::RINV + e * PT + q];
                 w1 = l1 * ratio;
@@ -481,8 +483,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const size_t ps = (size_t)s_item[pl].P;
                 const float *wf = reinterpret_cast<const float *>(sw + Z::WV);
                 const double *nut = sw + Z::NUT;
-                const float4 *eg = pd.eg2 + ps * pd_eg();
-                const float4 *eh = pd.eh2 + ps * pd_eg();
+                const float4 *eg = pd.eg2 + ps * pd_eg(pd.pmax);
+                const float4 *eh = pd.eh2 + ps * pd_eg(pd.pmax);
                 const bool hj = jk >= 3;
                 dfa Vr = {0, 0}, Vi = {0, 0}, Q0r = {0, 0}, Q0i = {0, 0}, Q1r = {0, 0}, Q1i = {0, 0}, Q2r = {0, 0}, Q2i = {0, 0};
                 dfa Q3r = {0, 0}, Q3i = {0, 0}, D0r = {0, 0}, D0i = {0, 0}, D1r = {0, 0}, D1i = {0, 0}, D2r = {0, 0}, D2i = {0, 0};
@@ -557,8 +559,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             double *sw = SW(pl);
             const size_t ps = (size_t)s_item[pl].P;
             const double *wv = sw + Z::WV, *nut = sw + Z::NUT;
-            const cd *eg = pd.eg + ps * pd_eg();
-            const cd *eh = pd.eh + ps * pd_eg();
+            const cd *eg = pd.eg + ps * pd_eg(pd.pmax);
+            const cd *eh = pd.eh + ps * pd_eg(pd.pmax);
             const bool hj = jk >= 3;
             double Vr = 0, Vi = 0;
             double Q0r = 0, Q0i = 0, Q1r = 0, Q1i = 0, Q2r = 0, Q2i = 0, Q3r = 0, Q3i = 0;
@@ -846,7 +848,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 // double-float dot products with the (hi, lo) fit matrices
                 dfa a0 = {0, 0}, a1 = {0, 0};
                 if (grp == 0) {
-                    const float2 *X = pd.XD2 + ps * pd_X();
+                    const float2 *X = pd.XD2 + ps * pd_X(pd.pmax);
                     const float2 *Bf = reinterpret_cast<const float2 *>(sw + Z::B), *Bdf = reinterpret_cast<const float2 *>(sw + Z::BD);
                     for (int lm = 0; lm < NP; lm++) {
                         const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
@@ -863,7 +865,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     r0 = dfval(a0);
                     r1 = dfval(a1) * sc;
                 } else if (grp == 1) {
-                    const float2 *X = pd.XSp2 + ps * pd_X(), *Bpf = reinterpret_cast<const float2 *>(sw + Z::DQ);
+                    const float2 *X = pd.XSp2 + ps * pd_X(pd.pmax), *Bpf = reinterpret_cast<const float2 *>(sw + Z::DQ);
                     for (int lm = 0; lm < NP; lm++)
                         for (int c = 0; c < 4; c++) {
                             const float2 x = X[(c * NP + lm) * NP + i], b = Bpf[4 * lm + c];
@@ -871,7 +873,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                         }
                     r0 = dfval(a0);
                 } else {
-                    const float2 *X = pd.XS22 + ps * pd_X(), *X1 = pd.XS12 + ps * pd_XS1();
+                    const float2 *X = pd.XS22 + ps * pd_X(pd.pmax), *X1 = pd.XS12 + ps * pd_XS1(pd.pmax);
                     const float2 *Bf = reinterpret_cast<const float2 *>(sw + Z::B), *Pf = reinterpret_cast<const float2 *>(sw + Z::PSI);
                     for (int lm = 0; lm < NP; lm++) {
                         const float2 x1 = X1[lm * NP + i], ps_ = Pf[lm];
@@ -885,7 +887,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     r0 = dfval(a0) * (1.0 / sc);
                 }
             } else if (grp == 0) {
-                const double *X = pd.XD + ps * pd_X(), *Bs = sw + Z::B, *Bds = sw + Z::BD;
+                const double *X = pd.XD + ps * pd_X(pd.pmax), *Bs = sw + Z::B, *Bds = sw + Z::BD;
                 for (int lm = 0; lm < NP; lm++) {
                     const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
                     const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
@@ -895,12 +897,12 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 }
                 r1 *= sc;
             } else if (grp == 1) {
-                const double *X = pd.XSp + ps * pd_X(), *Bp = sw + Z::DQ;
+                const double *X = pd.XSp + ps * pd_X(pd.pmax), *Bp = sw + Z::DQ;
                 for (int lm = 0; lm < NP; lm++)
                     r0 += Bp[4 * lm] * X[(0 * NP + lm) * NP + i] + Bp[4 * lm + 1] * X[(1 * NP + lm) * NP + i] +
                           Bp[4 * lm + 2] * X[(2 * NP + lm) * NP + i] + Bp[4 * lm + 3] * X[(3 * NP + lm) * NP + i];
             } else {
-                const double *X = pd.XS2 + ps * pd_X(), *X1 = pd.XS1 + ps * pd_XS1(), *Bs = sw + Z::B;
+                const double *X = pd.XS2 + ps * pd_X(pd.pmax), *X1 = pd.XS1 + ps * pd_XS1(pd.pmax), *Bs = sw + Z::B;
                 const double *Psis = sw + Z::PSI;
                 for (int lm = 0; lm < NP; lm++)
                     r0 += Psis[lm] * X1[lm * NP + i] -
@@ -954,8 +956,9 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
 
 // Step 5, complex preimage t0 of every (pair, edge): Newton on sum_a (y_a(t) - y'_a)^2
 // from the root of the straight chord (|dt| <= 1e-14 max(1,|t|), newton_max steps), Im t0 >= 0;
-// an edge whose chord root is outside 1.5 rho0 takes the upsampled rule and keeps the chord
-// root.  One thread per (pair, edge), so the Newton chains of many pairs overlap.
+// an edge for which a bound shows that no root lies in the ellipse E_rho0 takes the
+// upsampled rule without Newton and keeps the chord root.  One thread per (pair, edge), so
+// the Newton chains of many pairs overlap.
 template <int P>
 __global__ void __launch_bounds__(128) k_roots(const OrderTables *__restrict__ tab, const PairItem *__restrict__ items,
                                                int64_t nitems, PatchData pd, const double *__restrict__ txyz,
@@ -973,7 +976,7 @@ __global__ void __launch_bounds__(128) k_roots(const OrderTables *__restrict__ t
         yt[b] = fr[12] * sy;
     }
     double ce[3 * P];
-    for (int i = 0; i < 3 * P; i++) ce[i] = pd.ea[(size_t)im.P * pd_ea() + 3 * P * e + i];
+    for (int i = 0; i < 3 * P; i++) ce[i] = pd.ea[(size_t)im.P * pd_ea(pd.pmax) + 3 * P * e + i];
     double ym[3], yp[3];
     for (int a = 0; a < 3; a++) {
         double sp = 0, sm = 0;
@@ -992,11 +995,31 @@ __global__ void __launch_bounds__(128) k_roots(const OrderTables *__restrict__ t
     int conv = 0;
     bool skip = false;
     {
+        // Newton is skipped only where no root can lie in the Bernstein ellipse E_rho0, so that
+        // the rule is the one the root would select.  With the chord c + b t of the edge,
+        // f(t) = sum_a (y_a(t) - y'_a)^2 = |b|^2 (t - tt)(t - conj tt) + 2 (b t - w).d(t) + d.d,
+        // with d(t) = sum_{n >= 2} a_n (P_n(t) - e_n(t)) the deviation from the chord (e_n = 1
+        // for even n, t for odd n).  On and inside E_rho0: |P_n| <= rho0^n (Laplace's integral),
+        // |e_n| <= |t| <= A0 = (rho0 + 1/rho0)/2, so |d| <= D = sum_{n>=2} |a_n| (rho0^n + A0);
+        // and |t - tt| >= the gap between the
+        // confocal ellipses through tt and E_rho0, (rc + 1/rc - rho0 - 1/rho0)/2.  No root
+        // there if |b|^2 gap^2 > 2 (|b| A0 + |w|) D + D^2.
         const cd zm1 = mkc(tt.x - 1.0, tt.y), zp1 = mkc(tt.x + 1.0, tt.y);
         const cd wv = cadd(tt, cmul(sqrt_c(zm1), sqrt_c(zp1)));
         double rc = sqrt(cabs2(wv));
         if (rc < 1.0) rc = 1.0 / rc;
-        if (rc > 1.5 * tab->rho0 && tt.y > 0.0) { skip = true; conv = 1; }
+        const double r0 = tab->rho0, A0 = 0.5 * (r0 + 1.0 / r0);
+        if (rc > r0 && tt.y > 0.0) {
+            double D = 0.0, rn = r0;
+            for (int k = 2; k < P; k++) {
+                rn *= r0;
+                const double an = sqrt(ce[3 * k] * ce[3 * k] + ce[3 * k + 1] * ce[3 * k + 1] + ce[3 * k + 2] * ce[3 * k + 2]);
+                D += an * (rn + A0);
+            }
+            const double gap = 0.5 * (rc + 1.0 / rc - r0 - 1.0 / r0);
+            const double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+            if (bb * gap * gap > 2.0 * (sqrt(bb) * A0 + wn) * D + D * D) { skip = true; conv = 1; }
+        }
     }
     for (int it = 0; it < (skip ? 0 : newton_max); it++) {
         cd y[3], dy[3];
@@ -1047,7 +1070,7 @@ __global__ void __launch_bounds__(128) k_uside(const PairItem *__restrict__ item
             for (int a = 0; a < 3; a++) sy += fr[3 + 3 * a + b] * (txyz[3 * im.t + a] - fr[a]);
             yt[b] = fr[12] * sy;
         }
-        const double *xm = pd.xm + (size_t)im.P * pd_ynode();
+        const double *xm = pd.xm + (size_t)im.P * pd_ynode(pd.pmax);
         // vertices X(0,0) = xm[00], X(1,0) = sum_a xm[a0], X(0,1) = sum_b xm[0b]
         double v0[2] = {xm[0], xm[1]}, v1[2] = {0, 0}, v2[2] = {0, 0};
         {

@@ -128,7 +128,9 @@ struct PreSizes {
     static constexpr int HN_OFF = ASI_OFF + NP * NP;         // NP*NP
     static constexpr int TMP_OFF = HN_OFF + NP * NP;         // NP*NP
     static constexpr int TAB_OFF = TMP_OFF + NP * NP;        // NP*NJK complex (node tables)
-    static constexpr int PHASEB = TAB_OFF + 2 * NP * NJK;
+    // orders above 8: only the quaternion factor of the fit matrix stays in shared memory
+    static constexpr bool BIGP = P > 8;
+    static constexpr int PHASEB = BIGP ? 4 * NP * NP : TAB_OFF + 2 * NP * NJK;
     static constexpr int PHASEA = 2 * 3 * PT * NJK;          // edge tables
     static constexpr int BIG = PHASEB > PHASEA ? PHASEB : PHASEA;
     // persistent small arrays
@@ -144,6 +146,264 @@ struct PreSizes {
     static constexpr int TOTAL = LB_OFF + 4 * NP + 8;
     static constexpr size_t BYTES = sizeof(double) * TOTAL;
 };
+
+// (l, m) of the lm-th fit harmonic (l = 1..p, m = 1..l, l-major)
+__device__ __forceinline__ void lm_of(int lm, int &l, int &m) {
+    l = 1;
+    while ((l + 1) * l / 2 <= lm) l++;
+    m = lm - l * (l - 1) / 2 + 1;
+}
+
+// Steps 1-2 for orders above 8, where the 4 n_p x 4 n_p system no longer fits in shared memory
+// beside its right-hand sides: the quaternion matrix is factored in place in shared memory
+// (P A = L U, pivoting on the quaternion modulus, multipliers kept below the diagonal), and
+// each right-hand side is solved by one thread with its work vector in the output array
+// itself (X_D, X_S' in global memory, element (comp, row) of column c at
+// [(comp n_p + row) n_p + c], coalesced across threads).  The scalar SLP system is factored
+// the same way in the freed shared memory, its inverse solved into X_S1, and
+// X_S2 = X_D (Hn A_S^{-1}) formed from global memory.  Node harmonic tables are rebuilt per
+// node in per-thread local arrays where they are needed.
+template <int P>
+__device__ void fit_big(double *sm, const double *syn, const double *snl, const PatchData &pd, int pid, int tid,
+                        int nth, int &s_bad) {
+    constexpr int NP = P * (P + 1) / 2, NJK = (P + 1) * (P + 2) / 2;
+    const double sq2 = 1.4142135623730951;
+    q4 *Mq = reinterpret_cast<q4 *>(sm);  // [NP][NP]
+    __shared__ int s_pv[NP];
+    __shared__ double s_red[NP];
+    __shared__ double s_anorm;
+    __shared__ int s_k;
+    double *gXD = pd.XD + (size_t)pid * pd_X(pd.pmax), *gXSp = pd.XSp + (size_t)pid * pd_X(pd.pmax);
+    double *gXS2 = pd.XS2 + (size_t)pid * pd_X(pd.pmax), *gXS1 = pd.XS1 + (size_t)pid * pd_XS1(pd.pmax);
+    // the system matrix: row i (node), column lm, entry (0, grad H^{(l,m)}(y_i))
+    for (int i = tid; i < NP; i += nth) {
+        cd tb[NJK];
+        harmonic_table<P>(syn + 3 * i, tb);
+        for (int lm = 0; lm < NP; lm++) {
+            int l, m;
+            lm_of(lm, l, m);
+            cd g[3];
+            hgrad(tb, l, m, g);
+            q4 e = {0.0, sq2 * g[0].y, sq2 * g[1].y, sq2 * g[2].y};
+            Mq[i * NP + lm] = e;
+        }
+    }
+    __syncthreads();
+    // ||A||_1 (kappa_1 in the paper's normalisation, as for the lower orders)
+    if (pd.kappa) {
+        for (int lm = tid; lm < NP; lm += nth) {
+            double a = 0;
+            for (int i = 0; i < NP; i++) {
+                const q4 e = Mq[i * NP + lm];
+                a += fabs(e.x) + fabs(e.y) + fabs(e.z);
+            }
+            s_red[lm] = a * paper_norm(lm);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0;
+            for (int lm = 0; lm < NP; lm++) a = fmax(a, s_red[lm]);
+            s_anorm = a;
+        }
+    }
+    // factorisation
+    for (int k = 0; k < NP; k++) {
+        if (tid == 0) {
+            int pr = k;
+            double best = qnorm2(Mq[k * NP + k]);
+            for (int r = k + 1; r < NP; r++) {
+                const double v = qnorm2(Mq[r * NP + k]);
+                if (v > best) { best = v; pr = r; }
+            }
+            if (!(best > 0.0)) s_bad = 1;
+            s_pv[k] = pr;
+            s_k = pr;
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int pr = s_k;
+        if (pr != k)
+            for (int j = tid; j < NP; j += nth) {
+                const q4 t = Mq[k * NP + j];
+                Mq[k * NP + j] = Mq[pr * NP + j];
+                Mq[pr * NP + j] = t;
+            }
+        __syncthreads();
+        const q4 inv = qinv(Mq[k * NP + k]);
+        for (int r = k + 1 + tid; r < NP; r += nth) Mq[r * NP + k] = qmul(Mq[r * NP + k], inv);
+        __syncthreads();
+        const int w = NP - k - 1;
+        for (int f = tid; f < w * w; f += nth) {
+            const int r = k + 1 + f / w, j = k + 1 + f % w;
+            Mq[r * NP + j] = qsub(Mq[r * NP + j], qmul(Mq[r * NP + k], Mq[k * NP + j]));
+        }
+        __syncthreads();
+    }
+    if (!s_bad) {
+        // right-hand sides: column c < NP is (e_c, 0) [D], c >= NP is (0, nu_r e_r), r = c - NP [S']
+        for (int c = tid; c < 2 * NP; c += nth) {
+            double *X = c < NP ? gXD + c : gXSp + (c - NP);
+            const size_t cs = (size_t)NP * NP;  // stride between components
+            auto ld = [&](int row) {
+                q4 v = {X[(size_t)row * NP], X[cs + (size_t)row * NP], X[2 * cs + (size_t)row * NP],
+                        X[3 * cs + (size_t)row * NP]};
+                return v;
+            };
+            auto st = [&](int row, const q4 &v) {
+                X[(size_t)row * NP] = v.s;
+                X[cs + (size_t)row * NP] = v.x;
+                X[2 * cs + (size_t)row * NP] = v.y;
+                X[3 * cs + (size_t)row * NP] = v.z;
+            };
+            const int r0 = c < NP ? c : c - NP;
+            for (int row = 0; row < NP; row++) {
+                q4 v = {0.0, 0.0, 0.0, 0.0};
+                if (row == r0) {
+                    if (c < NP) v.s = 1.0;
+                    else { v.x = snl[3 * r0]; v.y = snl[3 * r0 + 1]; v.z = snl[3 * r0 + 2]; }
+                }
+                st(row, v);
+            }
+            // row interchanges in factorisation order, then L y = P b
+            for (int k = 0; k < NP; k++) {
+                const int pr = s_pv[k];
+                if (pr != k) {
+                    const q4 a = ld(k), b = ld(pr);
+                    st(k, b);
+                    st(pr, a);
+                }
+            }
+            for (int k = 0; k < NP; k++) {
+                const q4 yk = ld(k);
+                for (int r = k + 1; r < NP; r++) st(r, qsub(ld(r), qmul(Mq[r * NP + k], yk)));
+            }
+            // U x = y
+            for (int k = NP - 1; k >= 0; k--) {
+                q4 acc = ld(k);
+                for (int j = k + 1; j < NP; j++) acc = qsub(acc, qmul(Mq[k * NP + j], ld(j)));
+                st(k, qmul(qinv(Mq[k * NP + k]), acc));
+            }
+        }
+    }
+    __syncthreads();
+    // ||A^{-1}||_1 from the columns of X_D (as for the lower orders)
+    if (pd.kappa) {
+        for (int i = tid; i < NP; i += nth) {
+            double a = 0;
+            for (int c = 0; c < 4; c++)
+                for (int lm = 0; lm < NP; lm++) a += fabs(gXD[((size_t)c * NP + lm) * NP + i]) / paper_norm(lm);
+            s_red[i] = a;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0;
+            for (int i = 0; i < NP; i++) a = fmax(a, s_red[i]);
+            pd.kappa[pid] = (s_bad || !(a == a)) ? INFINITY : s_anorm * a;
+        }
+    }
+    // scalar SLP system A_S[i][lm] = grad H^{(l,m)}(y_i) . nu_i, factored in the freed space
+    double *AS = sm;
+    for (int i = tid; i < NP; i += nth) {
+        cd tb[NJK];
+        harmonic_table<P>(syn + 3 * i, tb);
+        const double *nu = snl + 3 * i;
+        for (int lm = 0; lm < NP; lm++) {
+            int l, m;
+            lm_of(lm, l, m);
+            cd g[3];
+            hgrad(tb, l, m, g);
+            AS[i * NP + lm] = sq2 * (g[0].y * nu[0] + g[1].y * nu[1] + g[2].y * nu[2]);
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < NP; k++) {
+        if (tid == 0) {
+            int pr = k;
+            double best = fabs(AS[k * NP + k]);
+            for (int r = k + 1; r < NP; r++)
+                if (fabs(AS[r * NP + k]) > best) { best = fabs(AS[r * NP + k]); pr = r; }
+            if (!(best > 0.0)) s_bad = 1;
+            s_pv[k] = pr;
+            s_k = pr;
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int pr = s_k;
+        if (pr != k)
+            for (int j = tid; j < NP; j += nth) {
+                const double t = AS[k * NP + j];
+                AS[k * NP + j] = AS[pr * NP + j];
+                AS[pr * NP + j] = t;
+            }
+        __syncthreads();
+        const double pinv = 1.0 / AS[k * NP + k];
+        for (int r = k + 1 + tid; r < NP; r += nth) AS[r * NP + k] *= pinv;
+        __syncthreads();
+        const int w = NP - k - 1;
+        for (int f = tid; f < w * w; f += nth) {
+            const int r = k + 1 + f / w, j = k + 1 + f % w;
+            AS[r * NP + j] -= AS[r * NP + k] * AS[k * NP + j];
+        }
+        __syncthreads();
+    }
+    if (!s_bad)
+        for (int c = tid; c < NP; c += nth) {
+            // column c of A_S^{-1} into X_S1[row][c]
+            double *X = gXS1 + c;
+            for (int row = 0; row < NP; row++) X[(size_t)row * NP] = row == c ? 1.0 : 0.0;
+            for (int k = 0; k < NP; k++) {
+                const int pr = s_pv[k];
+                if (pr != k) {
+                    const double a = X[(size_t)k * NP];
+                    X[(size_t)k * NP] = X[(size_t)pr * NP];
+                    X[(size_t)pr * NP] = a;
+                }
+            }
+            for (int k = 0; k < NP; k++) {
+                const double yk = X[(size_t)k * NP];
+                for (int r = k + 1; r < NP; r++) X[(size_t)r * NP] -= AS[r * NP + k] * yk;
+            }
+            for (int k = NP - 1; k >= 0; k--) {
+                double acc = X[(size_t)k * NP];
+                for (int j = k + 1; j < NP; j++) acc -= AS[k * NP + j] * X[(size_t)j * NP];
+                X[(size_t)k * NP] = acc / AS[k * NP + k];
+            }
+        }
+    __syncthreads();
+    // TMP = Hn A_S^{-1}, Hn[i][k] = sqrt2 Im S^{(l,m)}(y_i), in the freed space
+    double *TMP = sm;
+    for (int i = tid; i < NP; i += nth) {
+        cd tb[NJK];
+        harmonic_table<P>(syn + 3 * i, tb);
+        double hn[NP];
+        for (int k = 0; k < NP; k++) {
+            int l, m;
+            lm_of(k, l, m);
+            hn[k] = sq2 * tb[jk_index(l, m)].y;
+        }
+        for (int j = 0; j < NP; j++) {
+            double a = 0;
+            for (int k = 0; k < NP; k++) a += hn[k] * gXS1[(size_t)k * NP + j];
+            TMP[i * NP + j] = a;
+        }
+    }
+    __syncthreads();
+    // X_S2 = X_D TMP, and the double-float copies of the mixed path
+    for (int w = tid; w < 4 * NP * NP; w += nth) {
+        const int row = w / NP, i = w % NP;
+        double a = 0;
+        for (int k = 0; k < NP; k++) a += gXD[(size_t)row * NP + k] * TMP[k * NP + i];
+        gXS2[w] = a;
+        if (pd.XD2) {
+            const size_t o2 = (size_t)pid * pd_X(pd.pmax) + w;
+            pd.XD2[o2] = split2f(gXD[w]);
+            pd.XSp2[o2] = split2f(gXSp[w]);
+            pd.XS22[o2] = split2f(a);
+        }
+    }
+    if (pd.XS12)
+        for (int w = tid; w < NP * NP; w += nth) pd.XS12[(size_t)pid * pd_XS1(pd.pmax) + w] = split2f(gXS1[w]);
+}
 
 template <int P>
 __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restrict__ tab,
@@ -247,16 +507,16 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         sea[w] = s;
     }
     __syncthreads();
-    double *g_ea = pd.ea + (size_t)pid * pd_ea();
-    double *g_ey = pd.ey + (size_t)pid * pd_ey();
-    double *g_et = pd.et + (size_t)pid * pd_ey();
-    double *g_eyu = pd.eyu + (size_t)pid * pd_eyu();
-    double *g_yn = pd.ynode + (size_t)pid * pd_ynode();
+    double *g_ea = pd.ea + (size_t)pid * pd_ea(pd.pmax);
+    double *g_ey = pd.ey + (size_t)pid * pd_ey(pd.pmax);
+    double *g_et = pd.et + (size_t)pid * pd_ey(pd.pmax);
+    double *g_eyu = pd.eyu + (size_t)pid * pd_eyu(pd.pmax);
+    double *g_yn = pd.ynode + (size_t)pid * pd_ynode(pd.pmax);
     for (int w = tid; w < 9 * P; w += nth) g_ea[w] = sea[w];
     for (int w = tid; w < 9 * PT; w += nth) g_ey[w] = sey[w];
     for (int w = tid; w < 3 * NP; w += nth) g_yn[w] = syn[w];
     // monomial coefficients of the local node interpolant X(u, v) = sum_ab xm[ab] u^a v^b
-    double *g_xm = pd.xm + (size_t)pid * pd_ynode();
+    double *g_xm = pd.xm + (size_t)pid * pd_ynode(pd.pmax);
     for (int w = tid; w < 3 * NP; w += nth) {
         const int ab = w / 3, a = w % 3;
         double v = 0.0;
@@ -279,8 +539,8 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
     cd *etab = reinterpret_cast<cd *>(sm);  // phase A: [3PT][NJK]
     for (int q = tid; q < 3 * PT; q += nth) harmonic_table<P>(sey + 3 * q, etab + q * NJK);
     __syncthreads();
-    cd *g_eg = pd.eg + (size_t)pid * pd_eg();
-    cd *g_eh = pd.eh + (size_t)pid * pd_eg();
+    cd *g_eg = pd.eg + (size_t)pid * pd_eg(pd.pmax);
+    cd *g_eh = pd.eh + (size_t)pid * pd_eg(pd.pmax);
     __syncthreads();
     for (int w = tid; w < 3 * PT * NJK; w += nth) {
         int q = w / NJK, jk = w % NJK;
@@ -308,12 +568,13 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
             g_eg[(size_t)w * 3 + a] = g[a];
             g_eh[(size_t)w * 3 + a] = hv[a];
             if (pd.eg2) {
-                pd.eg2[(size_t)pid * pd_eg() + (size_t)w * 3 + a] = split4(g[a]);
-                pd.eh2[(size_t)pid * pd_eg() + (size_t)w * 3 + a] = split4(hv[a]);
+                pd.eg2[(size_t)pid * pd_eg(pd.pmax) + (size_t)w * 3 + a] = split4(g[a]);
+                pd.eh2[(size_t)pid * pd_eg(pd.pmax) + (size_t)w * 3 + a] = split4(hv[a]);
             }
         }
     }
     __syncthreads();
+    if constexpr (!Z::BIGP) {
     // Steps 1-2: fit systems.  Node harmonic tables first.
     double *M = sm + Z::M_OFF, *W = sm + Z::W_OFF, *AS = sm + Z::AS_OFF, *ASI = sm + Z::ASI_OFF;
     double *HN = sm + Z::HN_OFF, *TMP = sm + Z::TMP_OFF;
@@ -435,7 +696,8 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         }
     }
     // scalar fit: LU with partial pivoting on A_S, identity right-hand sides
-    for (int k = 0; k < NP && !s_bad; k++) {
+    // (the exit test reads s_bad only after a barrier, so that all threads leave together)
+    for (int k = 0; k < NP; k++) {
         if (tid == 0) {
             int pr = k;
             double best = fabs(AS[k * NP + k]);
@@ -445,6 +707,7 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
             s_piv = pr;
         }
         __syncthreads();
+        if (s_bad) break;
         const int pr = s_piv;
         if (pr != k)
             for (int j = tid; j < NP; j += nth) {
@@ -483,8 +746,8 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         TMP[w] = s;
     }
     __syncthreads();
-    double *gXD = pd.XD + (size_t)pid * pd_X(), *gXSp = pd.XSp + (size_t)pid * pd_X();
-    double *gXS2 = pd.XS2 + (size_t)pid * pd_X(), *gXS1 = pd.XS1 + (size_t)pid * pd_XS1();
+    double *gXD = pd.XD + (size_t)pid * pd_X(pd.pmax), *gXSp = pd.XSp + (size_t)pid * pd_X(pd.pmax);
+    double *gXS2 = pd.XS2 + (size_t)pid * pd_X(pd.pmax), *gXS1 = pd.XS1 + (size_t)pid * pd_XS1(pd.pmax);
     for (int w = tid; w < 4 * NP * NP; w += nth) {
         int row = w / NP, i = w % NP;       // row = comp * NP + lm
         int comp = row / NP, lm = row % NP;
@@ -496,7 +759,7 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
         for (int k = 0; k < NP; k++) s += W[4 * (lm * 2 * NP + k) + comp] * TMP[k * NP + i];
         gXS2[w] = s;
         if (pd.XD2) {
-            const size_t o2 = (size_t)pid * pd_X() + w;
+            const size_t o2 = (size_t)pid * pd_X(pd.pmax) + w;
             pd.XD2[o2] = split2f(qd[comp]);
             pd.XSp2[o2] = split2f(qs[comp]);
             pd.XS22[o2] = split2f(s);
@@ -504,7 +767,10 @@ __global__ void __launch_bounds__(256) k_precompute(const OrderTables *__restric
     }
     for (int w = tid; w < NP * NP; w += nth) {
         gXS1[w] = ASI[w];
-        if (pd.XS12) pd.XS12[(size_t)pid * pd_XS1() + w] = split2f(ASI[w]);
+        if (pd.XS12) pd.XS12[(size_t)pid * pd_XS1(pd.pmax) + w] = split2f(ASI[w]);
+    }
+    } else {
+        fit_big<P>(sm, syn, snl, pd, pid, tid, nth, s_bad);
     }
     if (tid == 0) pd.status[pid] = s_bad;
 }
@@ -534,6 +800,10 @@ cudaError_t rrq_launch_precompute(int p, const OrderTables *d_tab, const int32_t
         case 6: return launch_pre<6>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
         case 7: return launch_pre<7>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
         case 8: return launch_pre<8>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
+        case 9: return launch_pre<9>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
+        case 10: return launch_pre<10>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
+        case 11: return launch_pre<11>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
+        case 12: return launch_pre<12>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
         default: return cudaErrorInvalidValue;
     }
 }

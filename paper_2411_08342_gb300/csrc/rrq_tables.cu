@@ -141,22 +141,9 @@ int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, Orde
     gl_rule(pt, T->tq, T->wq);
     gl_rule(T->nup, T->tu, T->wu);
     gl_rule(RRQ_NOM, T->tom, T->wom);
-    // U[i][q]: coefficient of t^i in the Lagrange polynomial L_q(t)
-    for (int q = 0; q < pt; q++) {
-        std::vector<double> poly(pt, 0.0);
-        poly[0] = 1.0;
-        int deg = 0;
-        double den = 1.0;
-        for (int r = 0; r < pt; r++) {
-            if (r == q) continue;
-            // poly *= (t - t_r)
-            for (int i = deg + 1; i >= 1; i--) poly[i] = poly[i - 1] - T->tq[r] * poly[i];
-            poly[0] = -T->tq[r] * poly[0];
-            deg++;
-            den *= (T->tq[q] - T->tq[r]);
-        }
-        for (int i = 0; i < pt; i++) T->U[i * pt + q] = poly[i] / den;
-    }
+    // reciprocal node differences of the dual Bjorck-Pereyra Vandermonde solve (rrq_pairs.cuh)
+    for (int k = 0; k < pt; k++)
+        for (int i = 0; i < pt; i++) T->BPr[k * pt + i] = (i > k) ? 1.0 / (T->tq[i] - T->tq[i - k - 1]) : 0.0;
     // Lup[s][q] by the barycentric formula
     std::vector<double> bw(pt);
     for (int q = 0; q < pt; q++) {

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-PMAX = 8
+PMAX = 12
 S, D, SP, DP = 1, 2, 4, 8
 KERNEL_BITS = {"S": S, "D": D, "SP": SP, "DP": DP}
 KERNEL_SLOT = {"S": 0, "D": 1, "SP": 2, "DP": 3}

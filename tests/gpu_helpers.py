@@ -123,3 +123,52 @@ def gpu_build_sampled(ctx, d, tg, tsel, kernels=KINDS, **kw):
         del arrs
         torch.cuda.synchronize()
     return rowptr, col, vals, diag
+
+
+def compare_with_oracle(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_host=False, sampled=False):
+    """Build on the GPU, compare CSR structure exactly and values through the row and
+    apply gates against the oracle (all rows, the rows tsel, or with sampled=True only
+    the rows tsel copied back from a full-size build); returns (row errors, diag)."""
+    from paper_2411_08342_gb300 import workloads as W
+    if sampled:
+        # only the selected rows come back from the device; compare them directly
+        grp, gcol, gvals, diag = gpu_build_sampled(ctx, d, tg, tsel, kernels)
+        rowptr, col, vals, tsel = grp, gcol, gvals, np.asarray(tsel)
+    else:
+        rowptr, col, vals, diag = gpu_build(ctx, d, tg, kernels, on_host=on_host)
+    osf = oracle_lib.OracleSurface(d)
+    if sampled:
+        orp, ocol, ovals, _ = osf.csr_rows(tg, tsel, kernels=kernels)
+        sub = W.Targets(tg.xyz[tsel], tg.nrm[tsel], tg.self_node[tsel])
+    elif tsel is None:
+        orp, ocol, ovals, _ = osf.csr_rows(tg, kernels=kernels)
+        grp, gcol, gvals = rowptr, col, vals
+        sub = tg
+    else:
+        tsel = np.asarray(tsel)
+        orp, ocol, ovals, _ = osf.csr_rows(tg, tsel, kernels=kernels)
+        lens = rowptr[tsel + 1] - rowptr[tsel]
+        grp = np.zeros(len(tsel) + 1, np.int64)
+        np.cumsum(lens, out=grp[1:])
+        idx = np.concatenate([np.arange(rowptr[t], rowptr[t + 1]) for t in tsel]) if len(tsel) else np.zeros(0, int)
+        gcol = col[idx]
+        gvals = {k: vals[k][idx] for k in kernels}
+        sub = W.Targets(tg.xyz[tsel], tg.nrm[tsel], tg.self_node[tsel])
+    assert np.array_equal(grp, orp), "row pointers differ"
+    assert np.array_equal(gcol, ocol), "columns differ"
+    # the oracle's own rounding sensitivity on the same rows (rigidly rotated inputs)
+    d2, tg2 = rotated(d, tg)
+    _, _, rvals, _ = oracle_lib.OracleSurface(d2).csr_rows(tg2, tsel, kernels=kernels)
+    errs = {k: row_error(k, d, sub, orp, ocol, gvals[k], ovals[k]) for k in kernels}
+    erot = {k: row_error(k, d, sub, orp, ocol, rvals[k], ovals[k]) for k in kernels}
+    sigma = W.random_ylm_density(d.xyz, 8, seed=7)
+    eapp = {k: apply_error(k, d, sub, orp, ocol, gvals[k], ovals[k], sigma) for k in kernels}
+    eplain = {k: apply_error(k, d, sub, orp, ocol, gvals[k], ovals[k], sigma, plain=True) for k in kernels}
+    erapp = {k: apply_error(k, d, sub, orp, ocol, rvals[k], ovals[k], sigma) for k in kernels}
+    for k in kernels:
+        assert np.all(np.isfinite(gvals[k])), k
+        assert errs[k] <= max(TOL_E, ROT_FACTOR * erot[k]), (k, errs, erot)
+        assert eapp[k] <= max(TOL_APPLY, ROT_FACTOR * erapp[k]), (k, eapp, erapp)
+    print("row E", {k: f"{v:.1e}" for k, v in errs.items()}, "oracle self", {k: f"{v:.1e}" for k, v in erot.items()},
+          "apply", {k: f"{v:.1e}" for k, v in eapp.items()}, "apply plain", {k: f"{v:.1e}" for k, v in eplain.items()})
+    return errs, diag

@@ -88,29 +88,32 @@ def test_batch_equals_single_builds(ctx, batch_data, mixed, autotune):
 
 
 def test_batch_against_oracle(ctx, oracle_lib, batch_data):
-    """Surface 4 of the batch (320 patches, order 6, on-surface nodes) row by row against
-    the oracle.  (On the coarsest surfaces of this batch, 80 strongly curved patches, the
-    FP64 path and the oracle differ systematically by up to ~2e-10 per row for S and D,
-    while the rule itself is in error by ~1e-2 there: p~ = 2p edge nodes do not resolve
-    those edges.)"""
+    """Surfaces 2 (80 strongly curved patches, order 6) and 4 (320 patches, order 6) of the
+    batch, on-surface nodes, row by row against the oracle.  On the 80-patch surface the
+    edges are curved enough that a straight-chord estimate of the edge root misjudges the
+    rule; the rows agree only because the root-finding skips Newton solely where a bound
+    excludes a root from the singularity-swap ellipse."""
     st = [_surf_targ(ctx, d, tg) for d, tg in batch_data]
     b = ctx.batch([s for s, _ in st], [t for _, t in st])
     try:
         b.execute()
-        d, tg = batch_data[4]
-        assert d.p == 6 and d.npatch == 320
-        rowptr, col, vals = _view_host(ctx, b, 4)
+        got = {s: _view_host(ctx, b, s) for s in (2, 4)}
     finally:
         b.close()
-    osf = oracle_lib.OracleSurface(d)
-    orp, ocol, ovals, _ = osf.csr_rows(tg, kernels=KINDS)
-    assert np.array_equal(rowptr, orp) and np.array_equal(col, ocol)
-    d2, tg2 = rotated(d, tg)
-    _, _, rvals, _ = oracle_lib.OracleSurface(d2).csr_rows(tg2, kernels=KINDS)
-    for k in KINDS:
-        e = row_error(k, d, tg, orp, ocol, vals[k], ovals[k])
-        erot = row_error(k, d, tg, orp, ocol, rvals[k], ovals[k])
-        assert e <= max(TOL_E, ROT_FACTOR * erot), (k, e, erot)
+    for s in (2, 4):
+        d, tg = batch_data[s]
+        assert d.p == 6 and d.npatch == (80 if s == 2 else 320)
+        rowptr, col, vals = got[s]
+        osf = oracle_lib.OracleSurface(d)
+        orp, ocol, ovals, _ = osf.csr_rows(tg, kernels=KINDS)
+        assert np.array_equal(rowptr, orp) and np.array_equal(col, ocol)
+        d2, tg2 = rotated(d, tg)
+        _, _, rvals, _ = oracle_lib.OracleSurface(d2).csr_rows(tg2, kernels=KINDS)
+        for k in KINDS:
+            e = row_error(k, d, tg, orp, ocol, vals[k], ovals[k])
+            erot = row_error(k, d, tg, orp, ocol, rvals[k], ovals[k])
+            print(f"surface {s} {k}: E {e:.1e}, oracle self {erot:.1e}")
+            assert e <= max(TOL_E, ROT_FACTOR * erot), (s, k, e, erot)
 
 
 def test_batch_view_apply_and_errors(ctx, batch_data):

@@ -2,8 +2,9 @@
 kappa_1(A) per patch in the paper's harmonic normalisation (Sec. 5.1) against the
 oracle's, which comes from an explicit inverse of the real 4 n_p x 4 n_p block matrix.
 The GPU takes ||A||_1 from the harmonic gradients and ||A^{-1}||_1 from the quaternion
-solves of the fit; both inverses carry relative errors of about kappa x 1e-16, far below
-the 1e-8 allowed here."""
+solves of the fit.  Both inverses carry rounding errors that grow with kappa; the
+tolerance is max(1e-8, 1e-18 kappa) relative (at p = 12, kappa reaches 5e12 on the most
+curved paraboloid patch, where the two differ by 6e-7)."""
 import numpy as np
 import pytest
 
@@ -11,6 +12,10 @@ from paper_2411_08342_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-8
+
+
+def _tol(k):
+    return max(RTOL, 1e-18 * k)
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +38,7 @@ def _surface(ctx, d, on_host=False):
     return ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv), a
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 def test_kappa_paraboloid(ctx, oracle_lib, p):
     """Single paraboloid patches (eq. paraboloid) over curvatures and sizes."""
     for H, h in ((0.0, 1.0), (1.0, 1.0), (10.0, 1.0), (10.0, 0.125)):
@@ -42,7 +47,7 @@ def test_kappa_paraboloid(ctx, oracle_lib, p):
         k_gpu = float(ctx.fit_condition(s).cpu()[0])
         k_orc = oracle_lib.OracleSurface(d).patch_kappa(0)
         print(f"p={p} H={H} h={h}: kappa gpu {k_gpu:.6e} oracle {k_orc:.6e}")
-        assert abs(k_gpu - k_orc) <= RTOL * k_orc, (p, H, h, k_gpu, k_orc)
+        assert abs(k_gpu - k_orc) <= _tol(k_orc) * k_orc, (p, H, h, k_gpu, k_orc)
 
 
 @pytest.mark.parametrize("on_host", [False, True])

@@ -2,14 +2,13 @@
 
 CSR structure (row pointers, columns) must be identical; values must agree to
 E <= 1e-10 (see gpu_helpers.row_error).  Sizes span several tiles and ragged tails:
-orders 2..8, on-surface (self and near) and off-surface targets down to 1e-6 h.
+orders 2..8 (9..12 in test_gpu_high_order.py), on-surface (self and near) and off-surface targets down to 1e-6 h.
 """
 import numpy as np
 import pytest
 
 from paper_2411_08342_gb300 import workloads as W
-from tests.gpu_helpers import (KINDS, ROT_FACTOR, TOL_APPLY, TOL_E, apply_error, gpu_build, gpu_build_sampled,
-                               rotated, row_error)
+from tests.gpu_helpers import KINDS, compare_with_oracle as _compare, gpu_build
 
 pytestmark = pytest.mark.gpu
 
@@ -23,51 +22,6 @@ def ctx():
     c = rrq.Context(0)
     yield c
     c.close()
-
-
-def _compare(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_host=False, sampled=False):
-    if sampled:
-        # only the selected rows come back from the device; compare them directly
-        grp, gcol, gvals, diag = gpu_build_sampled(ctx, d, tg, tsel, kernels)
-        rowptr, col, vals, tsel = grp, gcol, gvals, np.asarray(tsel)
-    else:
-        rowptr, col, vals, diag = gpu_build(ctx, d, tg, kernels, on_host=on_host)
-    osf = oracle_lib.OracleSurface(d)
-    if sampled:
-        orp, ocol, ovals, _ = osf.csr_rows(tg, tsel, kernels=kernels)
-        sub = W.Targets(tg.xyz[tsel], tg.nrm[tsel], tg.self_node[tsel])
-    elif tsel is None:
-        orp, ocol, ovals, _ = osf.csr_rows(tg, kernels=kernels)
-        grp, gcol, gvals = rowptr, col, vals
-        sub = tg
-    else:
-        tsel = np.asarray(tsel)
-        orp, ocol, ovals, _ = osf.csr_rows(tg, tsel, kernels=kernels)
-        lens = rowptr[tsel + 1] - rowptr[tsel]
-        grp = np.zeros(len(tsel) + 1, np.int64)
-        np.cumsum(lens, out=grp[1:])
-        idx = np.concatenate([np.arange(rowptr[t], rowptr[t + 1]) for t in tsel]) if len(tsel) else np.zeros(0, int)
-        gcol = col[idx]
-        gvals = {k: vals[k][idx] for k in kernels}
-        sub = W.Targets(tg.xyz[tsel], tg.nrm[tsel], tg.self_node[tsel])
-    assert np.array_equal(grp, orp), "row pointers differ"
-    assert np.array_equal(gcol, ocol), "columns differ"
-    # the oracle's own rounding sensitivity on the same rows (rigidly rotated inputs)
-    d2, tg2 = rotated(d, tg)
-    _, _, rvals, _ = oracle_lib.OracleSurface(d2).csr_rows(tg2, tsel, kernels=kernels)
-    errs = {k: row_error(k, d, sub, orp, ocol, gvals[k], ovals[k]) for k in kernels}
-    erot = {k: row_error(k, d, sub, orp, ocol, rvals[k], ovals[k]) for k in kernels}
-    sigma = W.random_ylm_density(d.xyz, 8, seed=7)
-    eapp = {k: apply_error(k, d, sub, orp, ocol, gvals[k], ovals[k], sigma) for k in kernels}
-    eplain = {k: apply_error(k, d, sub, orp, ocol, gvals[k], ovals[k], sigma, plain=True) for k in kernels}
-    erapp = {k: apply_error(k, d, sub, orp, ocol, rvals[k], ovals[k], sigma) for k in kernels}
-    for k in kernels:
-        assert np.all(np.isfinite(gvals[k])), k
-        assert errs[k] <= max(TOL_E, ROT_FACTOR * erot[k]), (k, errs, erot)
-        assert eapp[k] <= max(TOL_APPLY, ROT_FACTOR * erapp[k]), (k, eapp, erapp)
-    print("row E", {k: f"{v:.1e}" for k, v in errs.items()}, "oracle self", {k: f"{v:.1e}" for k, v in erot.items()},
-          "apply", {k: f"{v:.1e}" for k, v in eapp.items()}, "apply plain", {k: f"{v:.1e}" for k, v in eplain.items()})
-    return errs, diag
 
 
 @pytest.mark.parametrize("p", [4, 5])
@@ -144,7 +98,7 @@ def test_bad_arguments(ctx):
     from paper_2411_08342_gb300 import rrq
     d, tg = W.sphere80(4)
     bad = d.order.copy()
-    bad[3] = 11
+    bad[3] = 13   # above the largest supported order
     arrs = {k: np.ascontiguousarray(v) for k, v in dict(node_off=d.node_off, xyz=d.xyz, nrm=d.nrm, wts=d.wts).items()}
     surf = ctx.surface(bad, arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
     targ = ctx.targets(np.ascontiguousarray(tg.xyz), np.ascontiguousarray(tg.nrm), np.ascontiguousarray(tg.self_node))

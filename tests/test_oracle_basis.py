@@ -140,6 +140,27 @@ def test_ssq_moments_against_adaptive_quadrature(oracle_lib, ab):
         assert abs(K[i] - rk) < 1e-11 * max(1.0, abs(K[0]))
 
 
+@pytest.mark.parametrize("ab", [(0.3, 0.05), (-0.9, 1e-4), (1.2, 0.02), (0.0, 0.7), (0.5, 1e-7)])
+def test_ssq_weights_high_order(oracle_lib, ab):
+    """The edge rule's singularity-swap weights lambda (V^T lambda = I, Sec. 3.4) integrate
+    f(t) / ((t-a)^2+b^2)^{m/2} for a smooth f to near machine precision up to pt = 28
+    nodes (order p = 14), although cond(V) reaches 1e10 there: the system is solved by a
+    backward stable method (Sec. 5.1).  A rule formed as U^T I with the explicit inverse U
+    loses ~8 digits at pt = 24 to cancellation.  Reference by the sinh substitution."""
+    O = oracle_lib
+    a, b = ab
+    f = lambda t: np.exp(t) * np.cos(2 * t)
+    lo, hi = math.asinh((-1 - a) / b), math.asinh((1 - a) / b)
+    r1 = quad(lambda s: f(a + b * math.sinh(s)), lo, hi, limit=500, epsabs=0, epsrel=1e-13)[0]
+    r3 = quad(lambda s: f(a + b * math.sinh(s)) / (b * math.cosh(s)) ** 2, lo, hi, limit=500, epsabs=0,
+              epsrel=1e-13)[0]
+    for pt in (20, 24, 28):
+        x, _ = O.gauss_legendre(pt)
+        l1, l3 = O.ssq_weights(pt, a, b)
+        assert abs(l1 @ f(x) - r1) <= 2e-13 * abs(r1), (pt, l1 @ f(x), r1)
+        assert abs(l3 @ f(x) - r3) <= 2e-13 * abs(r3), (pt, l3 @ f(x), r3)
+
+
 def test_bernstein_radius(oracle_lib):
     O = oracle_lib
     assert abs(O.bernstein_rho(0.3 + 0j) - 1.0) < 1e-14
