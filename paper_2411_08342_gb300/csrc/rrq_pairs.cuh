@@ -190,7 +190,7 @@ __device__ __forceinline__ void edge_eval_cplx(const double *ea, int p, cd t, cd
     if (p > 1)
         for (int a = 0; a < 3; a++) { y[a] = cadd(y[a], cscale(t, ea[3 + a])); dy[a].x += ea[3 + a]; }
     for (int n = 1; n + 1 < p; n++) {
-        cd Pn = cscale(csub(cscale(cmul(t, Pc), 2.0 * n + 1.0), cscale(Pm, (double)n)), 1.0 / (n + 1.0));
+        cd Pn = cscale(csub(cscale(cmul(t, Pc), 2.0 * n + 1.0), cscale(Pm, (double)n)), rcp_small(n + 1));
         cd dPn = cadd(dPm, cscale(Pc, 2.0 * n + 1.0));
         for (int a = 0; a < 3; a++) {
             y[a] = cadd(y[a], cscale(Pn, ea[3 * (n + 1) + a]));

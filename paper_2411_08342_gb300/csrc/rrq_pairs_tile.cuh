@@ -309,13 +309,19 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     K[0] = ((1 - a) / sp + (1 + a) / sm) / (bi * bi);
                     K[1] = (1.0 / sm - 1.0 / sp) + a * K[0];
                     for (int i = 0; i + 2 < PT; i++) K[i + 2] = J[i] + 2.0 * a * K[i + 1] - c0 * K[i];
-                    dual_vandermonde_solve<PT>(K, tab->tq, tab->BPr);   // K uses J: solve J after it
                 }
-                dual_vandermonde_solve<PT>(J, tab->tq, tab->BPr);      // moments -> weights lambda
             }
         }
         __syncthreads();
-        // G1: upsampled kernel values of the edges that take the direct rule
+        // singularity-swap weights lambda = V^{-T} (J or K) in place, one thread per
+        // (pair, edge, m); then G1: upsampled kernel values of the edges that take the
+        // direct rule (disjoint edges, same scratch)
+        if (tid < nt * 6) {
+            const int pl = tid / 6, e = (tid >> 1) % 3, m3 = tid & 1;
+            double *sw = SW(pl);
+            if (sw[Z::T0 + 4 * e + 3] != 0.0 && (m3 == 0 || wantDP))
+                dual_vandermonde_solve<PT>(sw + Z::MOM + 2 * NUP * e + m3 * PT, tab->tq, tab->BPr);
+        }
         for (int f = tid; f < nt * 3 * NUP; f += nth) {
             const int pl = f / (3 * NUP), rem = f % (3 * NUP), e = rem / NUP, s2 = rem % NUP;
             double *sw = SW(pl);
@@ -1031,7 +1037,8 @@ __global__ void __launch_bounds__(128) k_roots(const OrderTables *__restrict__ t
             gp = cadd(gp, cscale(cmul(r, dy[a]), 2.0));
         }
         if (gp.x == 0.0 && gp.y == 0.0) break;
-        const cd dt = cdivz(g, gp);
+        const double rq = 1.0 / (gp.x * gp.x + gp.y * gp.y);
+        const cd dt = mkc((g.x * gp.x + g.y * gp.y) * rq, (g.y * gp.x - g.x * gp.y) * rq);
         tt = csub(tt, dt);
         const double at2 = cabs2(tt);
         if (cabs2(dt) <= 1e-28 * (at2 > 1.0 ? at2 : 1.0)) { conv = 1; break; }
