@@ -204,8 +204,9 @@ rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag);
  *
  * It computes exactly what rrq_build_corrections computes, with the same kernels, but
  * takes every scratch buffer from one static device array of RRQ_STATIC_SCRATCH_BYTES
- * (64 MiB) that each GPU loading this library holds until the process exits; about
- * 0.35 MB per patch plus the near list fit in it (e.g. a few hundred patches), larger
+ * (64 MiB) that each GPU loading this library holds until the process exits; the
+ * per-patch data take about 0.15 MB at a largest order of 6, 0.35 MB at 8 and 1.3 MB at
+ * 12, plus the near list and the order tables (e.g. a few hundred patches), larger
  * problems are rejected with RRQ_ERR_ARG and a message in rrq_last_error().  It calls
  * no cudaMalloc, cudaFree or allocating library routine.
  *   - inputs: device pointers only (inputs_on_host = 1 is rejected);

@@ -1,13 +1,13 @@
-// Instantiation of the per-pair stage for patch order p = 8: tiles of 4, 2 pairs per CTA
+// Instantiation of the per-pair stage for patch order p = 8: tiles of 4, 3, 2 pairs per CTA
 // (the first is the default), FP64 and mixed line integrals.
 #include "rrq_pairs_tile.cuh"
 
 cudaError_t rrq_launch_pairs_p8(bool mixed, const PairArgs &a, const PairShape &shape, cudaStream_t st) {
-    return rrqk::launch_pairs_order<8, 4, 2>(mixed, a, shape, st);
+    return rrqk::launch_pairs_order<8, 4, 3, 2>(mixed, a, shape, st);
 }
 
 cudaError_t rrq_launch_pairs_eval_p8(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
-    return rrqk::launch_pairs_eval_order<8, 4, 2>(a, shape, st);
+    return rrqk::launch_pairs_eval_order<8, 4, 3, 2>(a, shape, st);
 }
 
-int rrq_pair_tiles_p8(int out[4]) { return rrqk::tiles_of<4, 2>(out); }
+int rrq_pair_tiles_p8(int out[4]) { return rrqk::tiles_of<4, 3, 2>(out); }
