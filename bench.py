@@ -239,9 +239,9 @@ def bench_gpu(args):
     else:
         e2e = e2e_leg(ctx, d, tg, nnz, dev, flush, args, world, total_entries)
     # roofline of the dominant kernel (the per-pair kernel), FP64 ALU bound.  DRAM traffic of
-    # k_pairs_tile<6, false, 4> on this workload from a one-pass ncu capture
+    # k_pairs_tile<6, false, 5> on this workload from a one-pass ncu capture
     # (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
-    traffic = 2_191_115_008 + 3_852_600_576
+    traffic = 2_132_489_728 + 3_820_851_968
     peak = ctx.fma_peak_tflops(fp32=False)
     peak32 = ctx.fma_peak_tflops(fp32=True)
     fpp = flops_per_pair(P)
@@ -262,7 +262,7 @@ def bench_gpu(args):
                    "l2": "512 MB flush between timed steps", "parallelism": f"weak x{world}"},
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "traffic_note": "bytes per launch of k_pairs_tile<6, false, 4>, one-pass ncu capture",
+                     "traffic": traffic, "traffic_note": "bytes per launch of k_pairs_tile<6, false, 5> (the autotuned FP64 shape), one-pass ncu capture",
                      "kernel": "k_roots<6> + k_uside<6> + k_pairs_tile<6, false, T> (one per-pair stage)",
                      "peak_note": "measured FP64 FMA peak (rrq_measure_fma_peak); FP32 FMA peak %.1f TFLOP/s" % peak32,
                      "flops_per_pair": fpp, "kernel_ms": pair_s * 1e3},
