@@ -94,6 +94,30 @@ def test_edge_cases(ctx, oracle_lib):
     _compare(ctx, oracle_lib, one, t1)
 
 
+def test_degenerate_patch(ctx):
+    """A patch whose nodes are collinear (zero area) is reported, not built: the build
+    returns "degenerate patch or singular fit" before any per-pair kernel runs, and the
+    fit conditioning of that patch is infinite while its neighbour's is finite."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    tris = np.array([[[0, 0, 0], [1.0, 0, 0], [0, 1.0, 0]], [[0, 0, 1.0], [1.0, 0, 1.0], [2.0, 0, 1.0]]])
+    d = W.discretize(W.flat_surface(tris), 4)
+    d.nrm = np.nan_to_num(d.nrm)            # the map has no normal on the degenerate patch
+    tg = W.Targets(np.array([[0.3, 0.3, 0.01], [0.2, 0.1, -0.02]]), np.array([[0, 0, 1.0], [0, 0, 1.0]]),
+                   np.array([-1, -1], np.int64))
+    a = rrq.device_inputs(d, tg)
+    surf = ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv)
+    targ = ctx.targets(a["txyz"], a["tnrm"], a["tself"])
+    with pytest.raises(rrq.RRQError, match="degenerate"):
+        ctx.build_corrections(surf, targ)
+    k = ctx.fit_condition(surf).cpu().numpy()
+    assert np.isfinite(k[0]) and np.isinf(k[1]), k
+    torch.cuda.synchronize()
+    # the context stays usable
+    d2, tg2 = W.sphere80(4)
+    assert gpu_build(ctx, d2, tg2)[3]["npairs"] > 0
+
+
 def test_bad_arguments(ctx):
     from paper_2411_08342_gb300 import rrq
     d, tg = W.sphere80(4)

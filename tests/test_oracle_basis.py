@@ -237,3 +237,45 @@ def test_fit_condition_paraboloid(oracle_lib):
         assert all(b < a for a, b in zip(seq, seq[1:])), (p, seq)
         assert abs(seq[-1] / flat[p - 2] - 1) < 0.03, (p, seq[-1], flat[p - 2])
         assert _paraboloid_kappa(O, 10.0, 1.0, p) > 10 * flat[p - 2]
+
+
+def test_quaternion_interpolation_converges(oracle_lib):
+    """The quaternion harmonic fit of Sec. 3.2 (eq. dlpdensitylinearsystem2) on a flat
+    equilateral triangle of side 1 centred at the origin, as in the interpolation study of
+    Sec. 5.1: the scalar part of q = sum_lm (0, grad H^{(l,m)}) c^{(l,m)} reproduces the
+    density at the nodes (collocation) and, for the analytic densities of that study,
+    converges geometrically in p away from the nodes."""
+    O = oracle_lib
+    R = 1 / np.sqrt(3)
+    ang = 0.5 * np.pi + 2 * np.pi * np.arange(3) / 3
+    tri = np.stack([R * np.cos(ang), R * np.sin(ang), np.zeros(3)], -1)[None]
+    rng = np.random.default_rng(0)
+    a, b = rng.random(2000), rng.random(2000)
+    sw = a + b > 1
+    a[sw], b[sw] = 1 - a[sw], 1 - b[sw]
+    V = tri[0]
+    pts = V[0] + a[:, None] * (V[1] - V[0]) + b[:, None] * (V[2] - V[0])
+    funcs = {"1/(x^2+y^2+0.5)": lambda x, y: 1 / (x * x + y * y + 0.5),
+             "cos(12x+12y+1)": lambda x, y: np.cos(12 * x + 12 * y + 1)}
+    err = {}
+    for p in (4, 6, 8, 10, 12):
+        d = W.discretize(W.flat_surface(tri), p)
+        info = O.OracleSurface(d).patch_internals(0)
+        npn = p * (p + 1) // 2
+        fr = info["frame"]
+        c0, Rm, s = fr[:3], fr[3:12].reshape(3, 3), fr[12]
+        XD = info["XD"].reshape(4, npn, npn)
+        for name, f in funcs.items():
+            mu = f(d.xyz[:, 0], d.xyz[:, 1])
+            c = np.einsum("qli,i->lq", XD, mu)
+            def q0(P):
+                _, gH = O.basis_batch(p, s * (P - c0) @ Rm)
+                return -np.einsum("mla,la->m", gH, c[:, 1:])
+            assert np.abs(q0(d.xyz) - mu).max() < 1e-9 * np.abs(mu).max(), (p, name)
+            ref = f(pts[:, 0], pts[:, 1])
+            err[(name, p)] = np.abs(q0(pts) - ref).max() / np.abs(ref).max()
+    e1 = [err[("1/(x^2+y^2+0.5)", p)] for p in (4, 6, 8, 10, 12)]
+    assert all(b_ < a_ / 3 for a_, b_ in zip(e1, e1[1:])), e1
+    assert e1[-1] < 1e-5, e1
+    e2 = [err[("cos(12x+12y+1)", p)] for p in (4, 6, 8, 10, 12)]
+    assert e2[-1] < e2[0] / 20, e2
