@@ -227,6 +227,23 @@ rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surface *surf, c
                                         int32_t *col, double *val[4], int64_t capacity, int64_t *nnz_out,
                                         int64_t *npairs_out);
 
+/* Build into caller-owned buffers that the device can address: device memory, managed
+ * memory, or page-locked host memory (cudaHostAlloc, or cudaHostRegister'ed and mapped),
+ * which the per-pair kernels then write directly, so that no copy of the matrices
+ * follows the build.  Same values as rrq_build_corrections (same kernels).
+ *   - rowptr [ntarg+1], col [capacity], val[k] [capacity] for every kernel k in
+ *     kernel_mask (the others may be NULL); CSR layout as rrq_csr;
+ *   - inputs as rrq_options.inputs_on_host says; other options as for a build;
+ *   - *nnz_out, *npairs_out (may be NULL): entries per kernel and near pairs.
+ * If an output buffer is not device-addressable (plain pageable host memory) nothing is
+ * launched and RRQ_ERR_ARG is returned; if the entries exceed capacity, *nnz_out is set,
+ * nothing beyond the near list is computed and RRQ_ERR_ARG is returned (call again with
+ * a larger capacity).  Synchronises the context stream. */
+rrq_status rrq_build_corrections_into(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
+                                      uint32_t kernel_mask, const rrq_options *opt, int64_t *rowptr,
+                                      int32_t *col, double *val[4], int64_t capacity, int64_t *nnz_out,
+                                      int64_t *npairs_out);
+
 /* ---- Batched build of many surfaces (the paper has no counterpart: it builds one
  * surface at a time).  A batch plan takes nsurf surfaces, each with its own targets,
  * patch counts and orders, and runs the same per-patch and per-pair computation as

@@ -577,6 +577,115 @@ extern "C" rrq_status rrq_evaluate_near(rrq_ctx *ctx, const rrq_surface *surf, c
     return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
 }
 
+namespace {
+
+// Device address of a caller buffer: itself for device or managed memory, the mapped
+// address for page-locked host memory; false for memory the device cannot address.
+bool device_address(void *p, void **dp) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *dp = p;
+        return true;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *dp = a.devicePointer;
+        return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" rrq_status rrq_build_corrections_into(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ,
+                                                 uint32_t kernel_mask, const rrq_options *opt, int64_t *rowptr,
+                                                 int32_t *col, double *val[4], int64_t capacity, int64_t *nnz_out,
+                                                 int64_t *npairs_out) {
+    if (!ctx || !rowptr || !col || !val || capacity < 0) return RRQ_ERR_ARG;
+    if (kernel_mask == 0 || (kernel_mask & ~15u)) return RRQ_ERR_ARG;
+    rrq_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    CK(cudaSetDevice(ctx->device));
+    // every output buffer must be addressable by the kernels that write it
+    void *d_col = nullptr, *d_val[4] = {nullptr, nullptr, nullptr, nullptr}, *d_rp = nullptr;
+    bool ok = device_address(col, &d_col) && device_address(rowptr, &d_rp);
+    for (int k = 0; k < 4 && ok; k++)
+        if (kernel_mask & (1u << k)) ok = val[k] && device_address(val[k], &d_val[k]);
+    if (!ok) {
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN,
+                 "rrq_build_corrections_into: an output buffer is neither device memory nor page-locked host memory");
+        return RRQ_ERR_ARG;
+    }
+    memset(&ctx->diag, 0, sizeof(ctx->diag));
+    rrq_launch_counter() = 0;
+    Scratch s;
+    s.st = ctx->stream;
+    Prep pr;
+    rrq_status rs = build_prep(ctx, s, surf, targ, o, false, pr);
+    if (rs != RRQ_OK) return rs;
+    if (nnz_out) *nnz_out = pr.nnz;
+    if (npairs_out) *npairs_out = pr.nb.npairs;
+    if (pr.nnz > capacity) {
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_into: %lld entries exceed the capacity %lld",
+                 (long long)pr.nnz, (long long)capacity);
+        return RRQ_ERR_ARG;
+    }
+    const NearBuffers &nb = pr.nb;
+    EdgeRoot *roots = (EdgeRoot *)Scratch::alloc(&s, sizeof(EdgeRoot) * 3 * (nb.npairs > 0 ? nb.npairs : 1));
+    int8_t *uside = (int8_t *)Scratch::alloc(&s, sizeof(int8_t) * (nb.npairs > 0 ? nb.npairs : 1));
+    unsigned long long *tile_ctr = (unsigned long long *)Scratch::alloc(&s, sizeof(unsigned long long) * (RRQ_PMAX + 1));
+    if (!roots || !uside || !tile_ctr) return RRQ_ERR_OOM;
+    cudaError_t e = cudaSuccess;
+    int start = 0;
+    for (int p = 2; p <= RRQ_PMAX && e == cudaSuccess; p++) {
+        const int n = (int)pr.plist[p].size();
+        if (n) {
+            const int64_t i0 = pr.h_roff[start], i1 = pr.h_roff[start + n];
+            PatchData pdo = pr.pd;
+            pdo.roots = roots + 3 * i0;
+            pdo.uside = uside + i0;
+            const PairArgs pa = {ctx->d_tab[p], pr.items + i0, i1 - i0, pdo, pr.in.node_off, pr.in.xyz, pr.in.nrm,
+                                 pr.in.wts, pr.in.txyz, pr.in.tnrm, pr.in.tself, kernel_mask, pr.newton_max,
+                                 {(double *)d_val[0], (double *)d_val[1], (double *)d_val[2], (double *)d_val[3]},
+                                 (int32_t *)d_col, pr.d_cnt};
+            const PairShape shape{ctx->tune_tile[pr.mixed][p], ctx->tune_pers[pr.mixed][p], tile_ctr + p};
+            e = rrq_launch_pairs(p, pr.mixed, pa, shape, s.st);
+        }
+        start += n;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], s.st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rowptr, pr.rowptr, sizeof(int64_t) * (pr.in.ntarg + 1), cudaMemcpyDefault, s.st);
+    BuildCounters hc;
+    memset(&hc, 0, sizeof(hc));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, pr.d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s.st);
+    if (e != cudaSuccess) {
+        set_err("pair kernel", e);
+        return RRQ_ERR_CUDA;
+    }
+    ctx->diag.npairs = nb.npairs;
+    ctx->diag.newton_fail = (int64_t)hc.newton_fail;
+    ctx->diag.on_edge = (int64_t)hc.on_edge;
+    ctx->diag.u_poor = (int64_t)hc.u_poor;
+    ctx->diag.ssq_edges = (int64_t)hc.ssq_edges;
+    ctx->diag.far_edges = (int64_t)hc.far_edges;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    ctx->diag.ms_precompute = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    ctx->diag.ms_near = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    ctx->diag.ms_pairs = ms;
+    ctx->diag.kernel_launches = rrq_launch_counter();
+    ctx->diag.kappa_max = pr.kappa_max;
+    return hc.newton_fail > 0 ? RRQ_WARN_ROOTFIND : RRQ_OK;
+}
+
 extern "C" rrq_status rrq_fit_condition(rrq_ctx *ctx, const rrq_surface *surf, double *kappa, int32_t on_host) {
     if (!ctx || !kappa) return RRQ_ERR_ARG;
     CK(cudaSetDevice(ctx->device));

@@ -93,6 +93,7 @@ def load(build_if_needed: bool = True):
                                                        C.c_uint32, C.POINTER(Options), C.c_void_p, C.c_void_p,
                                                        C.c_void_p * 4, C.c_int64, C.POINTER(C.c_int64),
                                                        C.POINTER(C.c_int64)]
+            L.rrq_build_corrections_into.argtypes = L.rrq_build_corrections_static.argtypes
             L.rrq_batch_create.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Surface), C.POINTER(TargetsS),
                                            C.c_uint32, C.POINTER(Options), C.c_uint32, C.POINTER(C.c_void_p)]
             L.rrq_batch_execute.argtypes = [C.c_void_p, C.c_void_p]
@@ -202,6 +203,27 @@ class Context:
         st = self.L.rrq_build_corrections_static(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt),
                                                  _ptr(rowptr), _ptr(col), arr, cap, C.byref(nnz), C.byref(npairs))
         _check(st, "rrq_build_corrections_static")
+        return nnz.value, npairs.value
+
+    def build_corrections_into(self, surf: Surface, targ: TargetsS, rowptr, col, vals: dict,
+                               kernels=("S", "D", "SP", "DP"), inputs_on_host: bool = False,
+                               mixed: bool = False, capacity: int = -1):
+        """Build into caller-owned buffers the device can address (torch CUDA tensors, or
+        page-locked host memory as numpy views of pinned tensors): rowptr [ntarg+1] int64,
+        col [capacity] int32, vals {kernel: [capacity] float64}.  The kernels write host
+        buffers directly (rrq_build_corrections_into).  Returns (nnz, npairs)."""
+        mask = 0
+        arr = (C.c_void_p * 4)()
+        for k in kernels:
+            mask |= KERNEL_BITS[k]
+            arr[KERNEL_SLOT[k]] = _ptr(vals[k]).value
+        cap = int(col.shape[0]) if capacity < 0 else capacity
+        nnz, npairs = C.c_int64(), C.c_int64()
+        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, int(mixed))
+        st = self.L.rrq_build_corrections_into(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt),
+                                               _ptr(rowptr), _ptr(col), arr, cap, C.byref(nnz), C.byref(npairs))
+        self.last_nnz = nnz.value
+        _check(st, "rrq_build_corrections_into")
         return nnz.value, npairs.value
 
     def batch(self, surfs, targs, kernels=("S", "D", "SP", "DP"), mixed: bool = False, autotune: bool = False,
