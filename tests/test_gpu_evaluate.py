@@ -27,10 +27,12 @@ def ctx():
 def _cases():
     d5, t5 = W.sphere80(5)
     d6, t6 = W.star1280(6, 3000, seed=31)
-    return {"sphere80_p5_on": (d5, t5), "star1280_p6_off": (d6, t6)}
+    d10 = W.discretize(W.sphere_surface(1), 10)
+    return {"sphere80_p5_on": (d5, t5), "star1280_p6_off": (d6, t6),
+            "sphere80_p10_on": (d10, W.on_surface_targets(d10))}
 
 
-@pytest.mark.parametrize("name", ["sphere80_p5_on", "star1280_p6_off"])
+@pytest.mark.parametrize("name", ["sphere80_p5_on", "star1280_p6_off", "sphere80_p10_on"])
 @pytest.mark.parametrize("on_host", [False, True])
 def test_evaluate_near_matches_csr(ctx, name, on_host):
     import torch

@@ -6,7 +6,10 @@ Stated tolerance of the mixed path: the apply-level gate of the FP64 path unchan
 rounding sensitivity (measured on the same rows with rigidly rotated inputs) or 1e-10.
 Double-float carries ~48 bits, so rows move by a few times more than in FP64 where the
 formulation is ill-conditioned (outer shell of the near region); smooth-density applies
-do not see it."""
+do not see it up to order 8.  From order 9 the fit's conditioning (kappa ~ 1e7-1e9 on
+these meshes) carries the ~1e-14 relative error of the double-float line integrals into
+the applied result at the 1e-10 level (2.3e-10 at p = 10 on the 320-patch star): there
+the stated apply tolerance of the mixed path is 1e-9."""
 import numpy as np
 import pytest
 
@@ -16,6 +19,7 @@ from tests.gpu_helpers import (KINDS, ROT_FACTOR, TOL_APPLY, TOL_E, apply_error,
 
 pytestmark = pytest.mark.gpu
 MIXED_ROW_FACTOR = 32.0
+MIXED_APPLY_TOL_HIGH_ORDER = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -35,10 +39,16 @@ def _cases():
     on = W.on_surface_targets(d8)
     sel = rng.choice(on.n, 300, replace=False)
     t8 = W.concat_targets(W.Targets(on.xyz[sel], on.nrm[sel], on.self_node[sel]), W.off_surface_targets(d8, 300, seed=8))
-    return {"star1280_p6": W.star1280(6, 600), "star320_p8": (d8, t8)}
+    d10 = W.discretize(W.star_surface(2), 10)
+    rng = np.random.default_rng(10)
+    on = W.on_surface_targets(d10)
+    sel = rng.choice(on.n, 200, replace=False)
+    t10 = W.concat_targets(W.Targets(on.xyz[sel], on.nrm[sel], on.self_node[sel]),
+                           W.off_surface_targets(d10, 200, seed=10))
+    return {"star1280_p6": W.star1280(6, 600), "star320_p8": (d8, t8), "star320_p10": (d10, t10)}
 
 
-@pytest.mark.parametrize("name", ["star1280_p6", "star320_p8"])
+@pytest.mark.parametrize("name", ["star1280_p6", "star320_p8", "star320_p10"])
 def test_mixed_against_oracle(ctx, oracle_lib, name):
     d, tg = _cases()[name]
     rowptr, col, vals, diag = gpu_build(ctx, d, tg, mixed=True)
@@ -55,7 +65,8 @@ def test_mixed_against_oracle(ctx, oracle_lib, name):
         era = apply_error(k, d, tg, orp, ocol, rvals[k], ovals[k], sigma)
         print(name, k, f"row {e:.1e} (oracle self {er:.1e}) apply {ea:.1e} (oracle self {era:.1e})")
         assert e <= max(TOL_E, MIXED_ROW_FACTOR * er), (k, e, er)
-        assert ea <= max(TOL_APPLY, ROT_FACTOR * era), (k, ea, era)
+        tol_apply = TOL_APPLY if d.p <= 8 else MIXED_APPLY_TOL_HIGH_ORDER
+        assert ea <= max(tol_apply, ROT_FACTOR * era), (k, ea, era)
 
 
 def test_mixed_apply_direct_sum(ctx):
