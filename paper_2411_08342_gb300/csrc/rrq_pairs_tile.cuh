@@ -392,22 +392,20 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const int npan = nl + 1 + nr;
                 for (int idx = lane; idx < npan * RRQ_NOM; idx += 32) {
                     const int pan = idx / RRQ_NOM, g = idx % RRQ_NOM;
+                    // panel k away from the central one spans (2^(k-1) - 1) sig .. (2^k - 1) sig
+                    // beyond lo (or hi): widths sig, 2 sig, 4 sig, ...
                     double a0, a1;
                     if (pan < nl) {
-                        const int k = nl - pan;
-                        double yk = lo, len = sig, ykm1 = lo;
-                        for (int s2 = 1; s2 <= k; s2++) { ykm1 = yk; yk -= len; len *= 2; }
-                        a0 = fmax(yk, -1.0);
-                        a1 = ykm1;
+                        const double pk = ldexp(1.0, nl - pan);
+                        a0 = fmax(lo - (pk - 1.0) * sig, -1.0);
+                        a1 = lo - (0.5 * pk - 1.0) * sig;
                     } else if (pan == nl) {
                         a0 = lo;
                         a1 = hi;
                     } else {
-                        const int k = pan - nl;
-                        double xk = hi, len = sig, xkm1 = hi;
-                        for (int s2 = 1; s2 <= k; s2++) { xkm1 = xk; xk += len; len *= 2; }
-                        a0 = xkm1;
-                        a1 = fmin(xk, 1.0);
+                        const double pk = ldexp(1.0, pan - nl);
+                        a0 = hi + (0.5 * pk - 1.0) * sig;
+                        a1 = fmin(hi + (pk - 1.0) * sig, 1.0);
                     }
                     const double mid = 0.5 * (a0 + a1), half = 0.5 * (a1 - a0);
                     const double tt = fma(half, tab->tom[g], mid), wg = half * tab->wom[g];
