@@ -279,3 +279,19 @@ def test_quaternion_interpolation_converges(oracle_lib):
     assert e1[-1] < 1e-5, e1
     e2 = [err[("cos(12x+12y+1)", p)] for p in (4, 6, 8, 10, 12)]
     assert e2[-1] < e2[0] / 20, e2
+
+
+def test_reference_rule_moments():
+    """The smooth rule of the synthetic inputs (workloads.ref_weights at workloads.ref_nodes)
+    integrates every monomial u^a v^b of total degree < p exactly over the reference
+    triangle (a! b! / (a + b + 2)!), to rounding, for every order up to 12; the nodes lie
+    strictly inside the triangle."""
+    for p in range(2, 13):
+        uv = W.ref_nodes(p)
+        w = W.ref_weights(p)
+        assert len(uv) == p * (p + 1) // 2
+        assert np.all(uv > 0) and np.all(uv.sum(1) < 1)
+        for a in range(p):
+            for b in range(p - a):
+                exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+                assert abs(np.sum(w * uv[:, 0] ** a * uv[:, 1] ** b) - exact) < 1e-15, (p, a, b)
