@@ -132,6 +132,15 @@ typedef struct {
                                 fit was singular */
 } rrq_diag;
 
+/* A reference node set for order p (2 <= p <= RRQ_PMAX) on the triangle
+ * {u, v >= 0, u + v <= 1}: uv [n_p][2], n_p = p(p+1)/2, the blend of the p Gauss-Legendre
+ * points of [0, 1] onto the triangle (strictly interior nodes, ordered i-major over the
+ * barycentric index triples i + j + k = p - 1), and, if w is not NULL, w [n_p] the
+ * interpolatory weights (exact for total degree < p, summing to 1/2).  Any other node set
+ * may be passed in rrq_surface.ref_uv; this one is what the test workloads use.  Host
+ * memory, no GPU work. */
+rrq_status rrq_ref_nodes(int32_t p, double *uv, double *w);
+
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream). */
 rrq_status rrq_ctx_create(rrq_ctx **ctx, int device, void *cuda_stream);

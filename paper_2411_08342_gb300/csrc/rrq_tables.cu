@@ -1,13 +1,14 @@
 // Per-order constant tables of librrq, computed once per order on the host.
 //
 //  * Gauss-Legendre rules (edge nodes t_q, the upsampled rule, the Omega_0 panel rule);
-//  * U: the inverse of the monomial Vandermonde matrix at the edge nodes (Sec. 3.4,
-//    c~ = U F), formed here by expanding the Lagrange polynomials in monomials;
+//  * the reciprocal node differences of the dual Vandermonde solve that turns the
+//    singularity-swap moments into weights (Sec. 3.4);
 //  * Lup: Lagrange basis of the edge nodes at the upsampled nodes (barycentric form);
 //  * Eint: the node interpolant evaluated at the edge samples and the vertices
 //    (Koornwinder-Dubiner basis on the reference triangle, solved with complete
 //    pivoting);
-//  * Legendre tables for the edge coefficients.
+//  * Legendre tables for the edge coefficients;
+//  * rrq_ref_nodes: a reference node set and its interpolatory weights for callers.
 #include <math.h>
 #include <string.h>
 
@@ -220,4 +221,32 @@ int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, Orde
         for (int i = 0; i < np * np; i++) T->Mmon[i] = I[i];
     }
     return 0;
+}
+
+extern "C" rrq_status rrq_ref_nodes(int32_t p, double *uv, double *w) {
+    if (p < 2 || p > RRQ_PMAX || !uv) return RRQ_ERR_ARG;
+    // 1-D Gauss-Legendre points on [0, 1], blended onto the triangle (i + j + k = p - 1)
+    double x[RRQ_PMAX], xw[RRQ_PMAX], g[RRQ_PMAX];
+    gl_rule(p, x, xw);
+    for (int i = 0; i < p; i++) g[i] = 0.5 * (x[i] + 1.0);
+    const int n = p - 1, np = p * (p + 1) / 2;
+    int r = 0;
+    for (int i = 0; i <= n; i++)
+        for (int j = 0; j <= n - i; j++, r++) {
+            const int k = n - i - j;
+            uv[2 * r] = (1.0 + 2.0 * g[j] - g[i] - g[k]) / 3.0;
+            uv[2 * r + 1] = (1.0 + 2.0 * g[k] - g[i] - g[j]) / 3.0;
+        }
+    if (!w) return RRQ_OK;
+    // interpolatory weights: V^T w = moments in the orthogonal basis (1/2 for the constant)
+    std::vector<double> VT(np * np), B(np, 0.0);
+    double psi[RRQ_NPMAX];
+    for (int i = 0; i < np; i++) {
+        dubiner_basis(n, uv[2 * i], uv[2 * i + 1], psi);
+        for (int b = 0; b < np; b++) VT[b * np + i] = psi[b];
+    }
+    B[0] = 0.5;
+    if (solve_complete_pivot(np, VT, 1, B)) return RRQ_ERR_ARG;
+    for (int i = 0; i < np; i++) w[i] = B[i];
+    return RRQ_OK;
 }

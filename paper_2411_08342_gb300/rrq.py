@@ -94,6 +94,7 @@ def load(build_if_needed: bool = True):
                                                        C.c_void_p * 4, C.c_int64, C.POINTER(C.c_int64),
                                                        C.POINTER(C.c_int64)]
             L.rrq_build_corrections_into.argtypes = L.rrq_build_corrections_static.argtypes
+            L.rrq_ref_nodes.argtypes = [C.c_int32, C.c_void_p, C.c_void_p]
             L.rrq_batch_create.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Surface), C.POINTER(TargetsS),
                                            C.c_uint32, C.POINTER(Options), C.c_uint32, C.POINTER(C.c_void_p)]
             L.rrq_batch_execute.argtypes = [C.c_void_p, C.c_void_p]
@@ -107,6 +108,14 @@ def load(build_if_needed: bool = True):
             L.rrq_fit_condition.argtypes = [C.c_void_p, C.POINTER(Surface), C.c_void_p, C.c_int32]
             _lib = L
     return _lib
+
+
+def ref_nodes(p: int):
+    """Reference nodes (n_p, 2) and interpolatory weights (n_p,) of order p (rrq_ref_nodes)."""
+    npn = p * (p + 1) // 2
+    uv, w = np.zeros((npn, 2)), np.zeros(npn)
+    _check(load().rrq_ref_nodes(p, uv.ctypes.data, w.ctypes.data), "rrq_ref_nodes")
+    return uv, w
 
 
 def _check(st: int, what: str):

@@ -42,3 +42,19 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not pat.search(txt), f
+
+
+def test_ref_nodes_host_function():
+    """rrq_ref_nodes (host code, no GPU): the same nodes and interpolatory weights as the
+    workload generator for every supported order, exact low-degree moments, and an
+    out-of-range order refused."""
+    import numpy as np
+    import pytest
+    from paper_2411_08342_gb300 import rrq, workloads as W
+    for p in range(2, 13):
+        uv, w = rrq.ref_nodes(p)
+        assert np.abs(uv - W.ref_nodes(p)).max() < 1e-15, p
+        assert np.abs(w - W.ref_weights(p)).max() < 1e-14, p
+        assert abs(w.sum() - 0.5) < 1e-15 and abs(w @ uv[:, 0] - 1 / 6) < 1e-15, p
+    with pytest.raises(rrq.RRQError, match="invalid argument"):
+        rrq.ref_nodes(13)
