@@ -522,9 +522,25 @@ def cpu_baseline(ntarg_sample: int) -> dict:
     entries = float(rowptr[-1]) * len(KERNELS)
     cores = len(os.sched_getaffinity(0))
     threads = int(os.environ.get("OMP_NUM_THREADS", cores))
-    return {"entries_per_s": entries / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {len(sel)} of the 200k targets, all near pairs, 4 kernels ({int(entries)} entries, "
-                      f"{dt:.1f} s)", "seconds": dt}
+    out = {"entries_per_s": entries / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"first {len(sel)} of the 200k targets, all near pairs, 4 kernels ({int(entries)} entries, "
+                     f"{dt:.1f} s)", "seconds": dt}
+    # one core, as the paper measures (its own Fortran on one EPYC core): a 16x smaller sample
+    try:
+        import ctypes
+        gomp = ctypes.CDLL("libgomp.so.1")
+        gomp.omp_set_num_threads(1)
+        sel1 = np.arange(max(1, len(sel) // 16))
+        t0 = time.perf_counter()
+        rp1, _, _, _ = osf.csr_rows(tg, sel1, KERNELS)
+        dt1 = time.perf_counter() - t0
+        gomp.omp_set_num_threads(threads)
+        e1 = float(rp1[-1]) * len(KERNELS)
+        out["one_core"] = {"entries_per_s": e1 / dt1, "points_per_s": len(sel1) / dt1,
+                           "sample": f"first {len(sel1)} targets ({int(e1)} entries, {dt1:.1f} s)"}
+    except OSError:
+        out["one_core"] = None
+    return out
 
 
 def bench_reference(args):
