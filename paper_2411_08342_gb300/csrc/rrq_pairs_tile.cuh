@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
     __shared__ int64_t s_base;
     __shared__ int s_self[T];
     __shared__ double s_uz[T];
+    __shared__ double s_h0[3 * T], s_h1[3 * T];  // Omega_0 and its nu' derivative per (pair, edge)
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const bool wantDP = (mask & RRQ_DP) != 0;
     // kernel groups of the row phase that this build needs
@@ -365,14 +366,45 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             sw[Z::OM3 + e * PT + q] = w3;
         }
         __syncthreads();
-        // H: Omega_0 (graded panels) and the Omega vector, warp per pair; premultiplied vectors
-        for (int pl = warp; pl < nt; pl += nwarp) {
+        // H, in three parts.  (1) premultiplied per-sample vectors w1 d, w1 (tau x d), w1 nu',
+        // w3 (nu'.d) d, one thread per (pair, sample)
+        for (int f = tid; f < nt * NS; f += nth) {
+            const int pl = f / NS, q = f % NS;
+            double *sw = SW(pl);
+            const double *nut = sw + Z::NUT, *dq = sw + Z::DQ, *tau = sw + Z::TAU;
+            const double w1 = sw[Z::OM1 + q], w3 = sw[Z::OM3 + q];
+            const double d0 = dq[3 * q], d1 = dq[3 * q + 1], d2 = dq[3 * q + 2];
+            const double t0 = tau[3 * q], t1 = tau[3 * q + 1], t2 = tau[3 * q + 2];
+            const double w3n = w3 * (nut[0] * d0 + nut[1] * d1 + nut[2] * d2);
+            double vv[12];
+            vv[0] = w1 * d0; vv[1] = w1 * d1; vv[2] = w1 * d2;
+            vv[3] = w1 * (t1 * d2 - t2 * d1); vv[4] = w1 * (t2 * d0 - t0 * d2); vv[5] = w1 * (t0 * d1 - t1 * d0);
+            vv[6] = w1; vv[7] = 0.0; vv[8] = 0.0;
+            vv[9] = w3n * d0; vv[10] = w3n * d1; vv[11] = w3n * d2;
+            double *wv = sw + Z::WV;
+            if (MIX) {
+                // the same 12 numbers as (hi, lo) float pairs, in the same slot
+                float *of = reinterpret_cast<float *>(wv + 12 * q);
+                for (int i = 0; i < 12; i++) {
+                    const float hi = __double2float_rn(vv[i]);
+                    of[2 * i] = hi;
+                    of[2 * i + 1] = __double2float_rn(vv[i] - (double)hi);
+                }
+            } else {
+                double *o = wv + 12 * q;
+                for (int i = 0; i < 12; i++) o[i] = vv[i];
+            }
+        }
+        // (2) Omega_0 on graded panels, one warp per (pair, edge), so that the warps share the
+        // edges evenly whatever the tile size; per-edge partial sums in shared memory
+        for (int pe = warp; pe < nt * 3; pe += nwarp) {
+            const int pl = pe / 3, e = pe % 3;
             double *sw = SW(pl);
             const double *yt = sw + Z::YT, *nut = sw + Z::NUT, *t0s = sw + Z::T0, *em = sw + Z::EM;
             const double uz = s_uz[pl];
             double o0 = 0.0, do0 = 0.0;
             const double nxu0 = uz * nut[1], nxu1 = -uz * nut[0], nuu = nut[2] * uz;
-            for (int e = 0; e < 3; e++) {
+            {
                 const double *cm = em + 3 * P * e;
                 const double tr = t0s[4 * e], ti = t0s[4 * e + 1];
                 double c, sig;
@@ -431,6 +463,18 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
             o0 = warp_sum(o0);
             if (wantDP) do0 = warp_sum(do0);
+            if (lane == 0) {
+                s_h0[pe] = o0;
+                s_h1[pe] = do0;
+            }
+        }
+        __syncthreads();
+        // (3) Omega_0 summed over the edges in order, the Omega vector, warp per pair
+        for (int pl = warp; pl < nt; pl += nwarp) {
+            double *sw = SW(pl);
+            const double *nut = sw + Z::NUT;
+            const double o0 = s_h0[3 * pl] + s_h0[3 * pl + 1] + s_h0[3 * pl + 2];
+            const double do0 = s_h1[3 * pl] + s_h1[3 * pl + 1] + s_h1[3 * pl + 2];
             const double *dq = sw + Z::DQ, *tau = sw + Z::TAU, *om1 = sw + Z::OM1, *om3 = sw + Z::OM3;
             double ov[3] = {0, 0, 0}, dov[3] = {0, 0, 0};
             for (int q = lane; q < NS; q += 32) {
@@ -448,31 +492,6 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 double *Om = sw + Z::OM;
                 Om[0] = o0; Om[1] = ov[0]; Om[2] = ov[1]; Om[3] = ov[2];
                 Om[4] = do0; Om[5] = dov[0]; Om[6] = dov[1]; Om[7] = dov[2];
-            }
-            // premultiplied per-sample vectors: w1 d, w1 (tau x d), w1 nu', w3 (nu'.d) d
-            double *wv = sw + Z::WV;
-            for (int q = lane; q < NS; q += 32) {
-                const double w1 = om1[q], w3 = om3[q];
-                const double d0 = dq[3 * q], d1 = dq[3 * q + 1], d2 = dq[3 * q + 2];
-                const double t0 = tau[3 * q], t1 = tau[3 * q + 1], t2 = tau[3 * q + 2];
-                const double w3n = w3 * (nut[0] * d0 + nut[1] * d1 + nut[2] * d2);
-                double vv[12];
-                vv[0] = w1 * d0; vv[1] = w1 * d1; vv[2] = w1 * d2;
-                vv[3] = w1 * (t1 * d2 - t2 * d1); vv[4] = w1 * (t2 * d0 - t0 * d2); vv[5] = w1 * (t0 * d1 - t1 * d0);
-                vv[6] = w1; vv[7] = 0.0; vv[8] = 0.0;
-                vv[9] = w3n * d0; vv[10] = w3n * d1; vv[11] = w3n * d2;
-                if (MIX) {
-                    // the same 12 numbers as (hi, lo) float pairs, in the same slot
-                    float *of = reinterpret_cast<float *>(wv + 12 * q);
-                    for (int i = 0; i < 12; i++) {
-                        const float hi = __double2float_rn(vv[i]);
-                        of[2 * i] = hi;
-                        of[2 * i + 1] = __double2float_rn(vv[i] - (double)hi);
-                    }
-                } else {
-                    double *o = wv + 12 * q;
-                    for (int i = 0; i < 12; i++) o[i] = vv[i];
-                }
             }
         }
         __syncthreads();
