@@ -241,7 +241,7 @@ def bench_gpu(args):
     # roofline of the dominant kernel (the per-pair kernel), FP64 ALU bound.  DRAM traffic of
     # k_pairs_tile<6, false, 5> on this workload from a one-pass ncu capture
     # (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
-    traffic = 2_145_442_560 + 3_823_211_520
+    traffic = 2_131_227_136 + 3_820_670_208
     peak = ctx.fma_peak_tflops(fp32=False)
     peak32 = ctx.fma_peak_tflops(fp32=True)
     fpp = flops_per_pair(P)
