@@ -146,7 +146,7 @@ def flops_per_pair(p: int) -> float:
     trans += np_ * 100                                 # I[gamma] and its nu' derivative per (l, m)
     # Step 8: per (node, (l, m)) 4-term dot products for D, D', S', S; jump and smooth rule per node
     rows = np_ * np_ * 34 + np_ * 60
-    weights = 3 * (pt * pt * 4 + pt * 30)              # lambda = U^T I for m = 1, 3 and the ratios
+    weights = 3 * (pt * pt * 4 + pt * 30)              # lambda = V^-T I for m = 1, 3 and the ratios
     moments = 3 * 20 * pt                              # J_i, K_i recurrences
     harm = ns * 12 + njk * (8 + 36)                    # samples, target table, gradients, Hessians
     u_choice = (np_ + ns) * 10

@@ -4,11 +4,12 @@
 //
 //   Step 4  harmonic table S^{(n,q)}(y'), its gradient (and Hessian for D') at the
 //           target in the patch frame;
-//   u       +e_z for a target that is a node of the patch, else the better of +-e_z
-//           by min over nodes and edge samples of u.(y'-y)/|y'-y|;
+//   u       +e_z for a target that is a node of the patch; else, if the target's
+//           footprint along e_z lies in the patch, the side it is on; else the better of
+//           +-e_z by min over nodes and edge samples of u.(y'-y)/|y'-y|;
 //   Step 5  per edge: complex root t0 of |y(t)-y'|^2 (Newton from the chord root),
-//           singularity-swap moments by recurrence and modified weights
-//           lambda = U^T I (Sec. 2.4, 3.4), or an upsampled Gauss rule when t0 is
+//           singularity-swap moments by recurrence and weights lambda solving
+//           V^T lambda = I (Sec. 2.4, 3.4), or an upsampled Gauss rule when t0 is
 //           outside the Bernstein ellipse of radius rho0;
 //           Omega_0 (eq. solidangle; its sign such that (1/4pi) d omega_0 =
 //           -grad G . nu da as Thm. dlp1form requires) on Gauss panels graded toward
