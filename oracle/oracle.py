@@ -1,8 +1,15 @@
-"""ctypes loader for the CPU FP64 oracle (rrq_oracle.c).
+"""ctypes loader for the CPU oracle (rrq_oracle.c).
 
 TEST INFRASTRUCTURE: only the tests, the smoke check and the CPU-baseline leg of
 the benchmark import this module.  The product path (the CUDA library and its
 binding) never does.
+
+The C source is compiled twice: the FP64 oracle (IEEE binary64 arithmetic) and, from
+the same source with -DORC_F128, an IEEE binary128 build of the same algorithm.  Both
+take and return binary64 arrays.  The binary128 build is the truth reference for the
+binary64 results: where a binary64 row differs from it, the difference is rounding (the
+algorithm and its discretisation are the same), so it measures how many digits of the
+RRQ row a binary64 implementation keeps.  Select it with ``ext=True``.
 """
 from __future__ import annotations
 
@@ -16,23 +23,35 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "librrq_oracle.so")
+_SO_EXT = os.path.join(_BUILD, "librrq_oracle_f128.so")
 _SRC = os.path.join(_HERE, "rrq_oracle.c")
 PMAX = 12
 KERNELS = ("S", "D", "SP", "DP")
 MASK = {"S": 1, "D": 2, "SP": 4, "DP": 8}
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, OpenMP)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+def _compile(so: str, defines, force: bool) -> str:
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", *defines,
                                "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+        os.replace(tmp, so)
+    return so
+
+
+def build(force: bool = False, ext: bool | None = None) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP): the binary64 build, and the binary128
+    build as well unless ext is False.  Returns the path of the build selected by ext
+    (binary64 when ext is None or False)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    so = _compile(_SO, [], force) if not ext else None
+    if ext is None or ext:
+        so_ext = _compile(_SO_EXT, ["-DORC_F128"], force)
+        if ext:
+            return so_ext
+    return so
 
 
 class _Opts(C.Structure):
@@ -40,19 +59,22 @@ class _Opts(C.Structure):
                 ("eta", C.c_double)]
 
 
-def lib():
-    global _lib
+def lib(ext: bool = False):
+    """The binary64 oracle, or with ext=True its binary128 build."""
     with _lock:
-        if _lib is None:
-            _lib = C.CDLL(build())
-            _lib.orc_surface_create.restype = C.c_void_p
-            _lib.orc_surface_destroy.argtypes = [C.c_void_p]
-            _lib.orc_T.restype = C.c_double
-            _lib.orc_patch_kappa.restype = C.c_double
+        L = _libs.get(ext)
+        if L is None:
+            L = C.CDLL(build(ext=ext))
+            L.orc_surface_create.restype = C.c_void_p
+            L.orc_surface_destroy.argtypes = [C.c_void_p]
+            L.orc_T.restype = C.c_double
+            L.orc_patch_kappa.restype = C.c_double
             for name in ("orc_near", "orc_rows", "orc_patch_internals", "orc_edge_root",
-                         "orc_pair_B", "orc_patch_bounds"):
-                getattr(_lib, name).restype = C.c_int
-    return _lib
+                         "orc_pair_B", "orc_patch_bounds", "orc_real_kind"):
+                getattr(L, name).restype = C.c_int
+            assert L.orc_real_kind() == (1 if ext else 0)
+            _libs[ext] = L
+    return L
 
 
 def _p(a):
@@ -63,8 +85,9 @@ class OracleSurface:
     """Holds a surface for the oracle.  Arrays are kept alive by this object."""
 
     def __init__(self, disc, ptilde: int = 0, rho0: float = 0.0, newton_max: int = 0,
-                 eta: float = 0.0):
-        L = lib()
+                 eta: float = 0.0, ext: bool = False):
+        L = self._L = lib(ext)
+        self.ext = ext
         self.d = disc
         self.order = np.ascontiguousarray(disc.order, dtype=np.int32)
         self.node_off = np.ascontiguousarray(disc.node_off, dtype=np.int64)
@@ -86,7 +109,7 @@ class OracleSurface:
     def __del__(self):
         try:
             if getattr(self, "h", None):
-                lib().orc_surface_destroy(C.c_void_p(self.h))
+                self._L.orc_surface_destroy(C.c_void_p(self.h))
                 self.h = None
         except Exception:
             pass
@@ -99,7 +122,7 @@ class OracleSurface:
         txyz = np.ascontiguousarray(targets.xyz, np.float64)
         tself = np.ascontiguousarray(targets.self_node, np.int64)
         counts = np.zeros(len(tsel), np.int64)
-        L = lib()
+        L = self._L
         L.orc_near(C.c_void_p(self.h), C.c_int64(len(tsel)), _p(tsel), _p(txyz), _p(tself),
                    _p(counts), None, None)
         offs = np.zeros(len(tsel) + 1, np.int64)
@@ -125,7 +148,7 @@ class OracleSurface:
             mask |= MASK[k]
         vals = {k: np.zeros(max(tot, 1)) for k in KERNELS}
         flags = np.zeros(max(npair, 1), np.int32)
-        L = lib()
+        L = self._L
         r = L.orc_rows(C.c_void_p(self.h), C.c_int64(npair), _p(pair_t), _p(pair_P),
                        _p(np.ascontiguousarray(targets.xyz, np.float64)),
                        _p(np.ascontiguousarray(targets.nrm, np.float64)),
@@ -159,7 +182,7 @@ class OracleSurface:
         out = dict(frame=np.zeros(13), vert=np.zeros(9), y=np.zeros(npn * 3), ea=np.zeros(9 * p),
                    ey=np.zeros(9 * pt), et=np.zeros(9 * pt), XD=np.zeros(4 * npn * npn),
                    XSp=np.zeros(4 * npn * npn), XS1=np.zeros(npn * npn), XS2=np.zeros(4 * npn * npn))
-        r = lib().orc_patch_internals(C.c_void_p(self.h), C.c_int(P), *[_p(out[k]) for k in
+        r = self._L.orc_patch_internals(C.c_void_p(self.h), C.c_int(P), *[_p(out[k]) for k in
                                       ("frame", "vert", "y", "ea", "ey", "et", "XD", "XSp", "XS1", "XS2")])
         out["status"] = r
         out["c"] = out["frame"][:3]
@@ -177,41 +200,41 @@ class OracleSurface:
 
     def patch_kappa(self, P: int) -> float:
         """1-norm condition number of patch P's fit matrix A (Sec. 5.1)."""
-        return float(lib().orc_patch_kappa(C.c_void_p(self.h), C.c_int(P)))
+        return float(self._L.orc_patch_kappa(C.c_void_p(self.h), C.c_int(P)))
 
     def pair_B(self, P: int, xt, nt, self_i: int = -1):
         p = int(self.order[P])
         npn = p * (p + 1) // 2
         B, dB, Psi, Om, dOm = np.zeros(4 * npn), np.zeros(4 * npn), np.zeros(npn), np.zeros(4), np.zeros(4)
-        fl = lib().orc_pair_B(C.c_void_p(self.h), C.c_int(P), _p(np.ascontiguousarray(xt, np.float64)),
+        fl = self._L.orc_pair_B(C.c_void_p(self.h), C.c_int(P), _p(np.ascontiguousarray(xt, np.float64)),
                               _p(np.ascontiguousarray(nt, np.float64)), C.c_int(self_i),
                               _p(B), _p(Psi), _p(dB), _p(Om), _p(dOm))
         return dict(B=B.reshape(npn, 4), Psi=Psi, dB=dB.reshape(npn, 4), Om=Om, dOm=dOm, flags=fl)
 
     def edge_root(self, P: int, e: int, yt):
         t0 = np.zeros(2)
-        c = lib().orc_edge_root(C.c_void_p(self.h), C.c_int(P), C.c_int(e),
+        c = self._L.orc_edge_root(C.c_void_p(self.h), C.c_int(P), C.c_int(e),
                                 _p(np.ascontiguousarray(yt, np.float64)), _p(t0))
         return complex(t0[0], t0[1]), bool(c)
 
 
 # ------------------------------------------------------------------ free functions
 
-def solid_S(L: int, y) -> np.ndarray:
+def solid_S(L: int, y, ext: bool = False) -> np.ndarray:
     out = np.zeros(2 * (L + 1) ** 2)
-    lib().orc_solid_S(C.c_int(L), _p(np.ascontiguousarray(y, np.float64)), _p(out))
+    lib(ext).orc_solid_S(C.c_int(L), _p(np.ascontiguousarray(y, np.float64)), _p(out))
     return out[0::2] + 1j * out[1::2]
 
 
-def solid_R(L: int, xyz) -> np.ndarray:
+def solid_R(L: int, xyz, ext: bool = False) -> np.ndarray:
     out = np.zeros(2 * (L + 1) ** 2)
-    lib().orc_solid_R(C.c_int(L), _p(np.ascontiguousarray(xyz, np.float64)), _p(out))
+    lib(ext).orc_solid_R(C.c_int(L), _p(np.ascontiguousarray(xyz, np.float64)), _p(out))
     return out[0::2] + 1j * out[1::2]
 
 
-def grad_hess_S(L: int, y, l: int, m: int):
+def grad_hess_S(L: int, y, l: int, m: int, ext: bool = False):
     g, H = np.zeros(6), np.zeros(18)
-    lib().orc_grad_hess_S(C.c_int(L), _p(np.ascontiguousarray(y, np.float64)), C.c_int(l), C.c_int(m),
+    lib(ext).orc_grad_hess_S(C.c_int(L), _p(np.ascontiguousarray(y, np.float64)), C.c_int(l), C.c_int(m),
                           _p(g), _p(H))
     return g[0::2] + 1j * g[1::2], (H[0::2] + 1j * H[1::2]).reshape(3, 3)
 
@@ -220,51 +243,51 @@ def hidx(n: int, q: int) -> int:
     return n * n + n + q
 
 
-def T(j, k, l, m) -> float:
-    return lib().orc_T(C.c_int(j), C.c_int(k), C.c_int(l), C.c_int(m))
+def T(j, k, l, m, ext: bool = False) -> float:
+    return lib(ext).orc_T(C.c_int(j), C.c_int(k), C.c_int(l), C.c_int(m))
 
 
-def gauss_legendre(n: int):
+def gauss_legendre(n: int, ext: bool = False):
     x, w = np.zeros(n), np.zeros(n)
-    lib().orc_gauss_legendre(C.c_int(n), _p(x), _p(w))
+    lib(ext).orc_gauss_legendre(C.c_int(n), _p(x), _p(w))
     return x, w
 
 
-def ssq_moments(n: int, a: float, b: float):
+def ssq_moments(n: int, a: float, b: float, ext: bool = False):
     J, K = np.zeros(n), np.zeros(n)
-    lib().orc_ssq_moments(C.c_int(n), C.c_double(a), C.c_double(b), _p(J), _p(K))
+    lib(ext).orc_ssq_moments(C.c_int(n), C.c_double(a), C.c_double(b), _p(J), _p(K))
     return J, K
 
 
-def ssq_weights(pt: int, a: float, b: float):
+def ssq_weights(pt: int, a: float, b: float, ext: bool = False):
     """Singularity-swap weights (m = 1, 3) at the pt Gauss-Legendre nodes for t0 = a + i b."""
     l1, l3 = np.zeros(pt), np.zeros(pt)
-    if lib().orc_ssq_weights(C.c_int(pt), C.c_double(a), C.c_double(b), _p(l1), _p(l3)):
+    if lib(ext).orc_ssq_weights(C.c_int(pt), C.c_double(a), C.c_double(b), _p(l1), _p(l3)):
         raise ValueError("bad arguments")
     return l1, l3
 
 
-def bernstein_rho(z: complex) -> float:
+def bernstein_rho(z: complex, ext: bool = False) -> float:
     r = C.c_double()
-    lib().orc_bernstein_rho(C.c_double(z.real), C.c_double(z.imag), C.byref(r))
+    lib(ext).orc_bernstein_rho(C.c_double(z.real), C.c_double(z.imag), C.byref(r))
     return r.value
 
 
-def lu_solve(A, B):
+def lu_solve(A, B, ext: bool = False):
     A = np.ascontiguousarray(A, np.float64)
     B = np.ascontiguousarray(B, np.float64).copy()
     nrhs = 1 if B.ndim == 1 else B.shape[1]
-    r = lib().orc_lu_solve(C.c_int(A.shape[0]), _p(A), C.c_int(nrhs), _p(B))
+    r = lib(ext).orc_lu_solve(C.c_int(A.shape[0]), _p(A), C.c_int(nrhs), _p(B))
     if r:
         raise np.linalg.LinAlgError("singular")
     return B
 
 
-def basis_batch(p: int, y):
+def basis_batch(p: int, y, ext: bool = False):
     """H^{(l,m)} and grad H^{(l,m)} (1 <= m <= l <= p) at points y (n, 3)."""
     y = np.ascontiguousarray(y, np.float64).reshape(-1, 3)
     npn = p * (p + 1) // 2
     H = np.zeros((len(y), npn))
     gH = np.zeros((len(y), npn, 3))
-    lib().orc_basis_batch(C.c_int(p), C.c_int64(len(y)), _p(y), _p(H), _p(gH))
+    lib(ext).orc_basis_batch(C.c_int(p), C.c_int64(len(y)), _p(y), _p(H), _p(gH))
     return H, gH
