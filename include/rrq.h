@@ -52,7 +52,9 @@ extern "C" {
 typedef int32_t rrq_status;
 enum {
     RRQ_OK = 0,
-    RRQ_ERR_ARG = -1,          /* NULL pointer, size or order out of range, NaN input */
+    RRQ_ERR_ARG = -1,          /* NULL pointer, size or order out of range, or a NaN or
+                                  infinity in the node positions, normals, weights, target
+                                  positions or target normals (checked on the device) */
     RRQ_ERR_CUDA = -2,         /* a CUDA call failed (message in rrq_last_error) */
     RRQ_ERR_OOM = -3,          /* device allocation failed */
     RRQ_ERR_DEGENERATE = -4,   /* a patch is degenerate or its fit matrix is singular */
@@ -219,13 +221,16 @@ rrq_status rrq_last_diagnostics(rrq_ctx *ctx, rrq_diag *diag);
  * problems are rejected with RRQ_ERR_ARG and a message in rrq_last_error().  It calls
  * no cudaMalloc, cudaFree or allocating library routine.
  *   - inputs: device pointers only (inputs_on_host = 1 is rejected);
+ *   - FP64 only: rrq_options.precision other than 0 gives RRQ_ERR_UNSUPPORTED; the
+ *     launch shapes are the orders' defaults (the context's tuned shapes are not used);
  *   - outputs (device, caller-owned): rowptr [ntarg+1], col [capacity], val[k]
  *     [capacity] for every kernel k in kernel_mask (S, D, S', D' order);
  *   - *nnz_out and *npairs_out (host, may be NULL) receive the entry and pair counts;
  *     when nnz exceeds capacity nothing is written to col/val and RRQ_ERR_ARG is
  *     returned with *nnz_out set, so the caller can retry with larger buffers;
- *   - the first call on a device looks up the array's device address (once per device,
- *     with that device current); make that first call before any stream capture;
+ *   - every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing), and reads sizes back to the host,
+ *     synchronising the context stream several times before it returns;
  *   - every call reuses the same array and leaves the last call's contents in it; what
  *     must start at zero is cleared by each call.  Calls whose GPU work overlaps (two
  *     streams, two threads, two contexts on one device) race on the array: serialise

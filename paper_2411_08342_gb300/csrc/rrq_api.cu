@@ -68,6 +68,41 @@ int rrq_pair_tiles(int p, int tiles[4]) {
     }
 }
 
+namespace {
+
+// Sets bit `bit` of *bad when a[0 .. n) holds a NaN or an infinity (grid-stride, one
+// warp vote per warp).
+__global__ void __launch_bounds__(256) k_nonfinite(const double *__restrict__ a, int64_t n, unsigned bit,
+                                                   unsigned *bad) {
+    bool any = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        any |= !isfinite(a[i]);
+    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, bit);
+}
+
+}  // namespace
+
+rrq_status check_finite(cudaStream_t st, unsigned *d_flag, const double *const arrays[], const int64_t sizes[],
+                        const char *const names[], int n) {
+    CK(cudaMemsetAsync(d_flag, 0, sizeof(unsigned), st));
+    for (int a = 0; a < n; a++) {
+        if (!arrays[a] || sizes[a] <= 0) continue;
+        const int64_t blocks = std::min<int64_t>((sizes[a] + 255) / 256, 152 * 4);
+        k_nonfinite<<<(unsigned)blocks, 256, 0, st>>>(arrays[a], sizes[a], 1u << a, d_flag);
+        RRQ_COUNT_LAUNCH();
+        CK(cudaGetLastError());
+    }
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int a = 0; a < n; a++)
+        if (h & (1u << a)) {
+            snprintf(rrq_err_buf(), RRQ_ERR_LEN, "non-finite value (NaN or infinity) in the %s", names[a]);
+            return RRQ_ERR_ARG;
+        }
+    return RRQ_OK;
+}
+
 rrq_status prepare_inputs(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const rrq_targets *targ, bool on_host,
                           bool need_targets, Inputs &in) {
     if (!surf || surf->npatch < 1 || !surf->order || !surf->node_off || !surf->xyz || !surf->nrm || !surf->wts)
@@ -113,7 +148,11 @@ rrq_status prepare_inputs(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, con
         set_err("input upload", err);
         return err == cudaErrorMemoryAllocation ? RRQ_ERR_OOM : RRQ_ERR_CUDA;
     }
-    return RRQ_OK;
+    unsigned *flag = (unsigned *)Scratch::alloc(&s, sizeof(unsigned));
+    if (!flag) return RRQ_ERR_OOM;
+    const double *arrays[5] = {in.xyz, in.nrm, in.wts, in.txyz, in.tnrm};
+    const int64_t sizes[5] = {3 * in.nnode, 3 * in.nnode, in.nnode, 3 * in.ntarg, 3 * in.ntarg};
+    return check_finite(s.st, flag, arrays, sizes, kInputNames, need_targets ? 5 : 3);
 }
 
 rrq_status order_tables(rrq_ctx *ctx, int p, const double *ref_uv, double rho0) {
@@ -1117,9 +1156,6 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_rrq_static_scratch[RRQ_STATIC_SCRATCH_BYTES];
 
-constexpr int RRQ_MAX_DEVICES = 64;
-static void *g_static_ptr[RRQ_MAX_DEVICES] = {nullptr};
-
 struct StaticArena {
     unsigned char *base;
     size_t used, cap;
@@ -1156,20 +1192,21 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
         snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: inputs must be device pointers");
         return RRQ_ERR_ARG;
     }
-    if (ctx->device < 0 || ctx->device >= RRQ_MAX_DEVICES) return RRQ_ERR_ARG;
+    if (o.precision != 0) {
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: FP64 only (precision = 0)");
+        return RRQ_ERR_UNSUPPORTED;
+    }
     const double eta = o.eta > 0 ? o.eta : 1.0;
     const int newton_max = o.newton_max > 0 ? o.newton_max : 30;
     CK(cudaSetDevice(ctx->device));
-    // set-up, once per device with that device current: device address of the array
-    if (!g_static_ptr[ctx->device]) {
-        void *p = nullptr;
-        CK(cudaGetSymbolAddress(&p, g_rrq_static_scratch));
-        g_static_ptr[ctx->device] = p;
-    }
+    // device address of the array on the current device, looked up on every call (no
+    // allocation; valid for the device's current context)
+    void *scratch_base = nullptr;
+    CK(cudaGetSymbolAddress(&scratch_base, g_rrq_static_scratch));
     memset(&ctx->diag, 0, sizeof(ctx->diag));
     rrq_launch_counter() = 0;
     StaticArena ar;
-    ar.base = static_cast<unsigned char *>(g_static_ptr[ctx->device]);
+    ar.base = static_cast<unsigned char *>(scratch_base);
     ar.used = 0;
     ar.cap = RRQ_STATIC_SCRATCH_BYTES;
     ar.failed = false;
@@ -1232,10 +1269,18 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     int32_t *d_plists = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);
     int32_t *d_rank = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);
     BuildCounters *d_cnt = (BuildCounters *)StaticArena::alloc(&ar, sizeof(BuildCounters));
+    unsigned *d_flag = (unsigned *)StaticArena::alloc(&ar, sizeof(unsigned));
     if (ar.failed) {
         snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: needs more than %zu bytes of scratch (maximum %zu)",
                  ar.wanted, (size_t)RRQ_STATIC_SCRATCH_BYTES);
         return RRQ_ERR_ARG;
+    }
+    {
+        const int64_t nnode = h_node_off[npatch];
+        const double *arrays[5] = {surf->xyz, surf->nrm, surf->wts, targ->xyz, targ->nrm};
+        const int64_t sizes[5] = {3 * nnode, 3 * nnode, nnode, 3 * ntarg, 3 * ntarg};
+        rrq_status rs = check_finite(st, d_flag, arrays, sizes, kInputNames, 5);
+        if (rs != RRQ_OK) return rs;
     }
     std::vector<int32_t> rank(npatch), order_major;
     order_major.reserve(npatch);

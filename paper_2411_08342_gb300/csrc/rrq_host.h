@@ -99,7 +99,16 @@ const T *upload(Scratch &s, const T *h, size_t n, bool on_host, cudaError_t *err
     return d;
 }
 
+// Checks the inputs and makes device views of them; a NaN or infinity in the node
+// positions, normals, weights, target positions or target normals gives RRQ_ERR_ARG.
 rrq_status prepare_inputs(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const rrq_targets *targ, bool on_host,
                           bool need_targets, Inputs &in);
+// One device pass over each of the n arrays (sizes in doubles); RRQ_ERR_ARG, with the
+// array's name in rrq_last_error(), if one holds a non-finite value.  d_flag: one
+// unsigned of device scratch.  Synchronises st.
+rrq_status check_finite(cudaStream_t st, unsigned *d_flag, const double *const arrays[], const int64_t sizes[],
+                        const char *const names[], int n);
+static const char *const kInputNames[5] = {"node positions", "node normals", "smooth weights", "target positions",
+                                          "target normals"};
 // per-order constant tables, cached in the context by (reference nodes, rho0)
 rrq_status order_tables(rrq_ctx *ctx, int p, const double *ref_uv, double rho0);

@@ -133,6 +133,44 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def _describe(a):
+    """(dtype name, element count, contiguous, device) of a torch tensor or numpy array;
+    device is ("cuda", index) or ("cpu", None)."""
+    if hasattr(a, "data_ptr"):
+        dev = (a.device.type, a.device.index if a.device.type == "cuda" else None)
+        return str(a.dtype).replace("torch.", ""), int(a.numel()), bool(a.is_contiguous()), dev
+    a = np.asarray(a)
+    return a.dtype.name, int(a.size), bool(a.flags.c_contiguous), ("cpu", None)
+
+
+def out_capacity(rowptr, col, vals: dict, kernels, ntarg: int, device: int, host_ok: bool) -> int:
+    """Checks the caller's CSR output buffers before any launch and returns the capacity
+    in entries: rowptr int64 with at least ntarg + 1 elements, col int32, vals[k] float64
+    for every requested kernel k, all contiguous, on cuda:device (or in host memory when
+    host_ok).  The capacity is the smallest of col's and every requested vals[k]'s
+    length, so the kernels never write past a buffer."""
+    def check(name, a, dtype, need=0):
+        if a is None:
+            raise RRQError(f"{name}: buffer missing")
+        dt, n, contig, dev = _describe(a)
+        if dt != dtype:
+            raise RRQError(f"{name}: dtype {dt}, expected {dtype}")
+        if not contig:
+            raise RRQError(f"{name}: not contiguous")
+        if dev[0] == "cuda" and dev[1] != device:
+            raise RRQError(f"{name}: on cuda:{dev[1]}, the context is on cuda:{device}")
+        if dev[0] != "cuda" and not host_ok:
+            raise RRQError(f"{name}: must be device memory")
+        if n < need:
+            raise RRQError(f"{name}: {n} elements, at least {need} needed")
+        return n
+    check("rowptr", rowptr, "int64", ntarg + 1)
+    cap = check("col", col, "int32")
+    for k in kernels:
+        cap = min(cap, check(f"vals[{k}]", vals.get(k), "float64"))
+    return cap
+
+
 class Context:
     """An rrq context bound to a CUDA device and stream (torch stream or raw handle)."""
 
@@ -201,12 +239,12 @@ class Context:
         """Allocation-free build into caller-owned device buffers (torch CUDA tensors):
         rowptr [ntarg+1] int64, col [capacity] int32, vals {kernel: [capacity] float64}.
         Returns (nnz, npairs)."""
+        cap = out_capacity(rowptr, col, vals, kernels, int(targ.ntarg), self.device, host_ok=False)
         mask = 0
         arr = (C.c_void_p * 4)()
         for k in kernels:
             mask |= KERNEL_BITS[k]
             arr[KERNEL_SLOT[k]] = vals[k].data_ptr()
-        cap = int(col.shape[0])
         nnz, npairs = C.c_int64(), C.c_int64()
         opt = Options(0, 0, 0.0, 0, 0.0, 0)
         st = self.L.rrq_build_corrections_static(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt),
@@ -221,12 +259,14 @@ class Context:
         page-locked host memory as numpy views of pinned tensors): rowptr [ntarg+1] int64,
         col [capacity] int32, vals {kernel: [capacity] float64}.  The kernels write host
         buffers directly (rrq_build_corrections_into).  Returns (nnz, npairs)."""
+        cap = out_capacity(rowptr, col, vals, kernels, int(targ.ntarg), self.device, host_ok=True)
+        if capacity >= 0:
+            cap = min(cap, capacity)
         mask = 0
         arr = (C.c_void_p * 4)()
         for k in kernels:
             mask |= KERNEL_BITS[k]
             arr[KERNEL_SLOT[k]] = _ptr(vals[k]).value
-        cap = int(col.shape[0]) if capacity < 0 else capacity
         nnz, npairs = C.c_int64(), C.c_int64()
         opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, int(mixed))
         st = self.L.rrq_build_corrections_into(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt),

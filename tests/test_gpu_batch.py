@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2411_08342_gb300 import workloads as W
-from tests.gpu_helpers import KINDS, ROT_FACTOR, TOL_E, gpu_build, rotated, row_error
+from tests.gpu_helpers import KINDS, TOL_E, TRUTH_FACTOR, fmt, gpu_build, row_error, truth_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -107,13 +107,12 @@ def test_batch_against_oracle(ctx, oracle_lib, batch_data):
         osf = oracle_lib.OracleSurface(d)
         orp, ocol, ovals, _ = osf.csr_rows(tg, kernels=KINDS)
         assert np.array_equal(rowptr, orp) and np.array_equal(col, ocol)
-        d2, tg2 = rotated(d, tg)
-        _, _, rvals, _ = oracle_lib.OracleSurface(d2).csr_rows(tg2, kernels=KINDS)
+        tr = truth_errors(oracle_lib, d, tg, None, orp, ocol, {"gpu": vals, "orc": ovals})
+        e64 = {k: row_error(k, d, tg, orp, ocol, vals[k], ovals[k]) for k in KINDS}
+        print(f"surface {s}: E_true gpu", fmt({k: v[0] for k, v in tr["gpu"].items()}),
+              "E_true fp64 oracle", fmt({k: v[0] for k, v in tr["orc"].items()}), "gpu vs fp64 oracle", fmt(e64))
         for k in KINDS:
-            e = row_error(k, d, tg, orp, ocol, vals[k], ovals[k])
-            erot = row_error(k, d, tg, orp, ocol, rvals[k], ovals[k])
-            print(f"surface {s} {k}: E {e:.1e}, oracle self {erot:.1e}")
-            assert e <= max(TOL_E, ROT_FACTOR * erot), (s, k, e, erot)
+            assert tr["gpu"][k][0] <= max(TOL_E, TRUTH_FACTOR * tr["orc"][k][0]), (s, k, tr["gpu"][k], tr["orc"][k])
 
 
 def test_batch_view_apply_and_errors(ctx, batch_data):

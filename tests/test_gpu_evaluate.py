@@ -1,14 +1,18 @@
 """Density-given near evaluation (rrq_evaluate_near): the correction applied to a density
-without storing the matrix (Sec. 4 Steps 1-8 with Step 2).  It must agree with the CSR
-of rrq_build_corrections times the same density, up to the different summation order
-(B . (X sigma) against sum_i (B . X_i) sigma_i): per target, |difference| <= 1e-12 x
-sum_j (|C_tj| + |K(t, x_j) w_j|) |sigma_j| over the row (the RRQ part and the smooth part
-it cancels are both summed)."""
+without storing the matrix (Sec. 4 Steps 1-8 with Step 2).
+
+* Against the CSR of rrq_build_corrections times the same density, up to the different
+  summation order (B . (X sigma) against sum_i (B . X_i) sigma_i): per target,
+  |difference| <= 1e-12 x sum_j (|C_tj| + |K(t, x_j) w_j|) |sigma_j| over the row (the RRQ
+  part and the smooth part it cancels are both summed).
+* Against the oracle, independently of the CUDA CSR: C_true sigma with C_true the rows of
+  the binary128 oracle, with the same normalisation; the gate is the apply gate of the
+  build, max(1e-10, TRUTH_FACTOR x the FP64 oracle's own C sigma error)."""
 import numpy as np
 import pytest
 
 from paper_2411_08342_gb300 import workloads as W
-from tests.gpu_helpers import KINDS, smooth_part
+from tests.gpu_helpers import KINDS, TOL_APPLY, TRUTH_FACTOR, fmt, smooth_part, truth_csr_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -70,6 +74,43 @@ def test_evaluate_near_matches_csr(ctx, name, on_host):
         err = np.max(np.abs(got[k] - ref) / scale)
         print(name, k, f"evaluate_near vs CSR: {err:.1e}")
         assert err <= 1e-12, (k, err)
+
+
+@pytest.mark.parametrize("name", ["sphere80_p5_on", "star1280_p6_off", "sphere80_p10_on"])
+def test_evaluate_near_against_oracle(ctx, oracle_lib, name):
+    """evaluate_near against C sigma of the oracle's rows (binary128 truth and FP64), on up
+    to 400 seeded targets of each case."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    d, tg = _cases()[name]
+    sig = W.random_ylm_density(d.xyz, 6, seed=5)
+    arrs = rrq.device_inputs(d, tg)
+    surf = ctx.surface(arrs["order"], arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
+    targ = ctx.targets(arrs["txyz"], arrs["tnrm"], arrs["tself"])
+    outs = {k: torch.zeros(tg.n, dtype=torch.float64, device="cuda") for k in KINDS}
+    ctx.evaluate_near(surf, targ, torch.as_tensor(sig, device="cuda"), outs)
+    got = {k: v.cpu().numpy() for k, v in outs.items()}
+    rng = np.random.default_rng(17)
+    tsel = np.sort(rng.choice(tg.n, min(tg.n, 400), replace=False))
+    sub = W.Targets(tg.xyz[tsel], tg.nrm[tsel], tg.self_node[tsel])
+    orp, ocol, ovals, _ = oracle_lib.OracleSurface(d).csr_rows(tg, tsel)
+    trp, tcol, tvals = truth_csr_rows(oracle_lib, d, tg, tsel)
+    assert np.array_equal(orp, trp) and np.array_equal(ocol, tcol)
+    nz = np.diff(orp) > 0
+    egpu, eorc = {}, {}
+    for k in KINDS:
+        sm = smooth_part(k, d, sub, orp, ocol)
+        scale = np.zeros(len(tsel))
+        ref, o64 = np.zeros(len(tsel)), np.zeros(len(tsel))
+        scale[nz] = np.add.reduceat((np.abs(tvals[k]) + np.abs(sm)) * np.abs(sig[ocol]), orp[:-1][nz])
+        ref[nz] = np.add.reduceat(tvals[k] * sig[ocol], orp[:-1][nz])
+        o64[nz] = np.add.reduceat(ovals[k] * sig[ocol], orp[:-1][nz])
+        egpu[k] = float(np.max(np.abs(got[k][tsel] - ref)[nz] / scale[nz]))
+        eorc[k] = float(np.max(np.abs(o64 - ref)[nz] / scale[nz]))
+        assert np.all(got[k][tsel][~nz] == 0.0), k
+    print(name, "evaluate_near vs binary128 C sigma", fmt(egpu), "FP64 oracle C sigma", fmt(eorc))
+    for k in KINDS:
+        assert egpu[k] <= max(TOL_APPLY, TRUTH_FACTOR * eorc[k]), (k, egpu[k], eorc[k])
 
 
 def test_evaluate_near_arguments(ctx):

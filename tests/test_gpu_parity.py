@@ -1,7 +1,8 @@
 """CUDA path (through the C ABI) against the CPU FP64 oracle, element by element.
 
-CSR structure (row pointers, columns) must be identical; values must agree to
-E <= 1e-10 (see gpu_helpers.row_error).  Sizes span several tiles and ragged tails:
+CSR structure (row pointers, columns) must be identical to the FP64 oracle's; values are
+gated against the binary128 build of the oracle (E_true <= max(1e-10, 4 x the FP64
+oracle's own E_true), see gpu_helpers).  Sizes span several tiles and ragged tails:
 orders 2..8 (9..12 in test_gpu_high_order.py), on-surface (self and near) and off-surface targets down to 1e-6 h.
 """
 import numpy as np
@@ -28,7 +29,7 @@ def ctx():
 def test_sphere80_all_rows(ctx, oracle_lib, p):
     """Unit sphere, 80 patches, all on-surface nodes, S D S' D'."""
     d, tg = W.sphere80(p)
-    errs, diag = _compare(ctx, oracle_lib, d, tg)
+    errs, diag = _compare(ctx, oracle_lib, d, tg, label=f"sphere80 p={p}", truth_max=800)
     assert diag["on_edge"] == 0
 
 
@@ -40,13 +41,13 @@ def test_orders_on_and_off_surface(ctx, oracle_lib, p):
     sel = rng.choice(on.n, min(on.n, 300), replace=False)
     tg = W.concat_targets(W.Targets(on.xyz[sel], on.nrm[sel], on.self_node[sel]),
                           W.off_surface_targets(d, 300, seed=p))
-    _compare(ctx, oracle_lib, d, tg)
+    _compare(ctx, oracle_lib, d, tg, label=f"star320 p={p}", truth_max=600 if p <= 5 else 200)
 
 
 def test_star1280_offsurface_p6(ctx, oracle_lib):
     """The star surface (1280 patches, p = 6) with 3000 targets at 10^-k h, k ~ U[0,6]."""
     d, tg = W.star1280(6, 3000)
-    _compare(ctx, oracle_lib, d, tg)
+    _compare(ctx, oracle_lib, d, tg, label="star1280 p=6 3000 targets")
 
 
 def test_host_inputs_same_as_device(ctx, oracle_lib):
@@ -130,13 +131,37 @@ def test_bad_arguments(ctx):
         ctx.build_corrections(surf, targ, inputs_on_host=True)
 
 
+@pytest.mark.parametrize("where", ["node", "normal", "weight", "target", "target_normal"])
+def test_nonfinite_inputs_rejected(ctx, where):
+    """A NaN (or infinity) in any floating-point input array is an argument error found
+    by one device pass before the build, with the array named; the context stays usable."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    d, tg = W.sphere80(4)
+    a = rrq.device_inputs(d, tg)
+    key, idx, val = {"node": ("xyz", 123, float("nan")), "normal": ("nrm", 7, float("nan")),
+                     "weight": ("wts", 799, float("inf")), "target": ("txyz", 2, float("nan")),
+                     "target_normal": ("tnrm", 2399, float("-inf"))}[where]
+    a[key].view(-1)[idx] = val
+    surf = ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv)
+    targ = ctx.targets(a["txyz"], a["tnrm"], a["tself"])
+    with pytest.raises(rrq.RRQError, match="non-finite"):
+        ctx.build_corrections(surf, targ)
+    with pytest.raises(rrq.RRQError, match="non-finite"):
+        out = {"D": torch.zeros(tg.n, dtype=torch.float64, device="cuda")}
+        ctx.evaluate_near(surf, targ, torch.ones(d.nnode, dtype=torch.float64, device="cuda"), out)
+    torch.cuda.synchronize()
+    d2, tg2 = W.sphere80(4)
+    assert gpu_build(ctx, d2, tg2)[3]["npairs"] > 0
+
+
 def test_full_size_sampled_rows(ctx, oracle_lib):
     """The benchmark workload (star, 1280 patches, p = 6, 200k targets) built in full
     on the GPU, with 200 seeded rows checked against the oracle."""
     d, tg = W.star1280(6, 200_000)
     rng = np.random.default_rng(11)
     tsel = np.sort(rng.choice(tg.n, 200, replace=False))
-    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel)
+    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, label="star1280 p=6 200k targets (benchmark)")
     assert diag["npairs"] > 200_000 * 10
 
 
@@ -148,7 +173,7 @@ def test_full_size_torus_p8_sampled(ctx, oracle_lib):
     non = d.nnode
     rng = np.random.default_rng(12)
     tsel = np.sort(np.concatenate([rng.choice(non, 60, replace=False), non + rng.choice(tg.n - non, 60, replace=False)]))
-    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, sampled=True)
+    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, sampled=True, label="wavy torus p=8")
     assert diag["npairs"] > 10_000_000
 
 
@@ -158,7 +183,7 @@ def test_full_size_ellipsoid_sampled(ctx, oracle_lib):
     d, tg = W.ellipsoid81920()
     rng = np.random.default_rng(13)
     tsel = np.sort(rng.choice(tg.n, 100, replace=False))
-    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, sampled=True)
+    errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, sampled=True, label="ellipsoid 81920 p=6")
     assert diag["npairs"] > 20_000_000
 
 

@@ -73,3 +73,31 @@ def test_static_rejects_problems_beyond_its_scratch():
                                      torch.empty(16, dtype=torch.int32, device=dev),
                                      {k: torch.empty(16, dtype=torch.float64, device=dev) for k in KINDS}, KINDS)
     ctx.close()
+
+
+def test_static_rejects_mixed_precision():
+    """The allocation-free build is FP64 only: a request for the mixed path is refused
+    (unsupported option) rather than silently built in FP64."""
+    import torch
+
+    from paper_2411_08342_gb300 import rrq
+    ctx = rrq.Context(0)
+    d, tg = W.sphere80(4)
+    a = rrq.device_inputs(d, tg)
+    surf = ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv)
+    targ = ctx.targets(a["txyz"], a["tnrm"], a["tself"])
+    dev = torch.device("cuda", 0)
+    rowptr = torch.empty(tg.n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(16, dtype=torch.int32, device=dev)
+    vals = {k: torch.empty(16, dtype=torch.float64, device=dev) for k in KINDS}
+    arr = (rrq.C.c_void_p * 4)()
+    for k in KINDS:
+        arr[rrq.KERNEL_SLOT[k]] = vals[k].data_ptr()
+    opt = rrq.Options(0, 0, 0.0, 0, 0.0, 1)
+    nnz, npairs = rrq.C.c_int64(), rrq.C.c_int64()
+    st = ctx.L.rrq_build_corrections_static(ctx.h, rrq.C.byref(surf), rrq.C.byref(targ), 15, rrq.C.byref(opt),
+                                            rrq._ptr(rowptr), rrq._ptr(col), arr, 16, rrq.C.byref(nnz),
+                                            rrq.C.byref(npairs))
+    assert ctx.L.rrq_status_string(st).decode() == "unsupported option"
+    assert "FP64 only" in ctx.L.rrq_last_error().decode()
+    ctx.close()
