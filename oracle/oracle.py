@@ -25,7 +25,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "librrq_oracle.so")
 _SO_EXT = os.path.join(_BUILD, "librrq_oracle_f128.so")
 _SRC = os.path.join(_HERE, "rrq_oracle.c")
-PMAX = 12
+PMAX = 14
 KERNELS = ("S", "D", "SP", "DP")
 MASK = {"S": 1, "D": 2, "SP": 4, "DP": 8}
 _lock = threading.Lock()

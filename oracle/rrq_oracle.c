@@ -93,7 +93,7 @@ typedef double complex cplx;
 #define xconj conj
 #endif
 
-#define ORC_PMAX 12
+#define ORC_PMAX 14
 #define ORC_LMAX 16
 #define ORC_PTMAX 32
 #define ORC_NOM 16
