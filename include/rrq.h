@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define RRQ_PMAX 12
+#define RRQ_PMAX 14
 
 typedef int32_t rrq_status;
 enum {
@@ -127,7 +127,8 @@ typedef struct {
     int64_t far_edges;       /* edges evaluated by the upsampled Gauss rule */
     double ms_near, ms_precompute, ms_pairs;  /* stage times of the last build (ms) */
     int64_t kernel_launches; /* CUDA kernels the last build launched */
-    double ms_apply_smooth, ms_apply_spmv;    /* kernel times of the last rrq_apply (ms) */
+    double ms_apply_smooth, ms_apply_spmv;    /* kernel time of the last rrq_apply and of the
+                                                 last rrq_apply_correction (ms) */
     double kappa_max;        /* largest 1-norm condition number kappa_1(A) of a patch's fit
                                 matrix A (eq. dlpdensitylinearsystem2) in the last build, in
                                 the paper's harmonic normalisation (Sec. 5.1); INFINITY if a
@@ -173,13 +174,27 @@ rrq_status rrq_csr_free(rrq_ctx *ctx, rrq_csr *csr);
 /* Apply one corrected operator (Sec. 5, eq. dlpsplitting):
  *   out[t] = sum_{j : x_j != target t} K(x_t, x_j) w_j density[j] + sum_j C[t][j] density[j]
  * with K the kernel `kernel` (one of RRQ_S, RRQ_D, RRQ_SP, RRQ_DP) and C its correction
- * CSR.  density [nnode] and out [ntarg] follow inputs_on_host.  The smooth sum is a
- * direct O(ntarg * nnode) sum (no fast multipole method); with rrq_options.precision = 1
- * it runs in FP32 (coordinates as (hi, lo) FP32 pairs so that x_t - x_j keeps ~1e-7
- * relative accuracy, kernel values in FP32, compensated FP32 sums per tile of 256
- * sources, FP64 across tiles), the correction SpMV stays FP64. */
+ * CSR (NULL: the smooth sum alone).  density [nnode] and out [ntarg] follow
+ * inputs_on_host.  One fused kernel: each block of targets sums the smooth rule over all
+ * nodes (a direct O(ntarg * nnode) sum; no fast multipole method) and then adds its
+ * targets' CSR rows.  With rrq_options.precision = 1 the smooth terms of nodes at least
+ * r_c from the target run in FP32 (coordinates as (hi, lo) FP32 pairs so that x_t - x_j
+ * keeps ~1e-7 relative accuracy, compensated FP32 sums per tile of sources, FP64 across
+ * tiles) and the closer ones, which all lie in the target's CSR row, in FP64 with the
+ * row (r_c = eta x the smallest node spread of a patch; the CSR is then required).
+ * rrq_last_diagnostics reports the kernel time as ms_apply_smooth. */
 rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, int32_t kernel,
                      const rrq_csr *corr, const double *density, double *out, const rrq_options *opt);
+
+/* The correction alone (Sec. 5, eq. dlpsplitting: the sparse part that is added to a
+ * smooth-rule sum computed elsewhere, e.g. by a fast multipole method):
+ *   out[t] = (accumulate ? out[t] : 0) + sum_j C[t][j] density[j],   t < corr->nrows,
+ * with C the CSR of `kernel` in corr (a build's CSR or a batch view).  density [nnode]
+ * (nnode > every column index) and out [nrows] are host memory when on_host != 0, else
+ * device memory.  One warp per row; HBM bound.  Synchronises the context stream;
+ * rrq_last_diagnostics reports the kernel time as ms_apply_spmv. */
+rrq_status rrq_apply_correction(rrq_ctx *ctx, const rrq_csr *corr, int32_t kernel, const double *density,
+                                int64_t nnode, double *out, int32_t accumulate, int32_t on_host);
 
 /* Density-given near evaluation (Sec. 4 Steps 1-8 with Step 2 for a given density, as the
  * paper evaluates close targets without storing the matrix):

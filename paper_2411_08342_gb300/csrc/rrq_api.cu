@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "rrq_host.h"
@@ -33,6 +34,8 @@ RRQ_DECL_PAIRS(9)
 RRQ_DECL_PAIRS(10)
 RRQ_DECL_PAIRS(11)
 RRQ_DECL_PAIRS(12)
+RRQ_DECL_PAIRS(13)
+RRQ_DECL_PAIRS(14)
 #undef RRQ_DECL_PAIRS
 
 cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape shape, cudaStream_t st) {
@@ -40,7 +43,7 @@ cudaError_t rrq_launch_pairs(int p, bool mixed, const PairArgs &a, PairShape sha
 #define RRQ_CASE(P) \
     case P: return rrq_launch_pairs_p##P(mixed, a, shape, st);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
-        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12)
+        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12) RRQ_CASE(13) RRQ_CASE(14)
 #undef RRQ_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -51,7 +54,7 @@ cudaError_t rrq_launch_pairs_eval(int p, const PairArgs &a, PairShape shape, cud
 #define RRQ_CASE(P) \
     case P: return rrq_launch_pairs_eval_p##P(a, shape, st);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
-        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12)
+        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12) RRQ_CASE(13) RRQ_CASE(14)
 #undef RRQ_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -62,7 +65,7 @@ int rrq_pair_tiles(int p, int tiles[4]) {
 #define RRQ_CASE(P) \
     case P: return rrq_pair_tiles_p##P(tiles);
         RRQ_CASE(2) RRQ_CASE(3) RRQ_CASE(4) RRQ_CASE(5) RRQ_CASE(6) RRQ_CASE(7) RRQ_CASE(8)
-        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12)
+        RRQ_CASE(9) RRQ_CASE(10) RRQ_CASE(11) RRQ_CASE(12) RRQ_CASE(13) RRQ_CASE(14)
 #undef RRQ_CASE
         default: return 0;
     }
@@ -70,25 +73,42 @@ int rrq_pair_tiles(int p, int tiles[4]) {
 
 namespace {
 
-// Sets bit `bit` of *bad when a[0 .. n) holds a NaN or an infinity (grid-stride, one
-// warp vote per warp).
-__global__ void __launch_bounds__(256) k_nonfinite(const double *__restrict__ a, int64_t n, unsigned bit,
-                                                   unsigned *bad) {
+constexpr int kMaxChecked = 8;
+struct CheckedArrays {
+    const double *a[kMaxChecked];
+    int64_t n[kMaxChecked];
+    int count;
+};
+
+// Sets bit k of *bad when array k holds a NaN or an infinity: blockIdx.y selects the
+// array, grid-stride over its elements, one warp vote per warp.
+__global__ void __launch_bounds__(256) k_nonfinite(CheckedArrays arr, unsigned *bad) {
+    const int k = blockIdx.y;
+    const double *__restrict__ a = arr.a[k];
+    const int64_t n = a ? arr.n[k] : 0;
     bool any = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         any |= !isfinite(a[i]);
-    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, bit);
+    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u << k);
 }
 
 }  // namespace
 
 rrq_status check_finite(cudaStream_t st, unsigned *d_flag, const double *const arrays[], const int64_t sizes[],
                         const char *const names[], int n) {
-    CK(cudaMemsetAsync(d_flag, 0, sizeof(unsigned), st));
+    if (n > kMaxChecked) return RRQ_ERR_ARG;
+    CheckedArrays arr{};
+    int64_t most = 0;
     for (int a = 0; a < n; a++) {
-        if (!arrays[a] || sizes[a] <= 0) continue;
-        const int64_t blocks = std::min<int64_t>((sizes[a] + 255) / 256, 152 * 4);
-        k_nonfinite<<<(unsigned)blocks, 256, 0, st>>>(arrays[a], sizes[a], 1u << a, d_flag);
+        arr.a[a] = sizes[a] > 0 ? arrays[a] : nullptr;
+        arr.n[a] = sizes[a];
+        most = std::max(most, sizes[a]);
+    }
+    arr.count = n;
+    CK(cudaMemsetAsync(d_flag, 0, sizeof(unsigned), st));
+    if (most > 0) {
+        const int64_t blocks = std::min<int64_t>((most + 255) / 256, 152 * 2);
+        k_nonfinite<<<dim3((unsigned)blocks, (unsigned)n), 256, 0, st>>>(arr, d_flag);
         RRQ_COUNT_LAUNCH();
         CK(cudaGetLastError());
     }
@@ -278,6 +298,7 @@ void alloc_patch_data(Scratch &s, size_t NPc, bool mixed, PatchData &pd) {
     pd.XS1 = (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_XS1(pd.pmax));
     pd.status = (int *)Scratch::alloc(&s, sizeof(int) * NPc);
     pd.kappa = (double *)Scratch::alloc(&s, sizeof(double) * NPc);
+    pd.lu = pd_lu(pd.pmax) ? (double *)Scratch::alloc(&s, sizeof(double) * NPc * pd_lu(pd.pmax)) : nullptr;
 }
 
 rrq_status build_prep(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const rrq_targets *targ, const rrq_options &o,
@@ -801,66 +822,25 @@ extern "C" rrq_status rrq_csr_free(rrq_ctx *ctx, rrq_csr *csr) {
 }
 
 // ------------------------------------------------------------------------------------
-// Apply: smooth direct sum over all nodes (sources staged in shared memory) + SpMV.
+// Apply (Sec. 5, eq. dlpsplitting): smooth direct sum over all nodes plus the correction
+// row, fused in one kernel per tile of targets; and the correction alone (SpMV).
 // ------------------------------------------------------------------------------------
 namespace {
 
 constexpr int APPLY_TILE = 256;
+constexpr double kInv4Pi = 0.07957747154594767;
 
-__global__ void __launch_bounds__(APPLY_TILE) k_apply(int kernel, const double *__restrict__ xyz, const double *__restrict__ nrm,
-                                                      const double *__restrict__ wts, const double *__restrict__ sig,
-                                                      int64_t nnode, const double *__restrict__ txyz,
-                                                      const double *__restrict__ tnrm, const int64_t *__restrict__ tself,
-                                                      int64_t ntarg, double *__restrict__ out) {
-    __shared__ double sx[APPLY_TILE * 3], sn[APPLY_TILE * 3], sw[APPLY_TILE];
-    const int64_t t = (int64_t)blockIdx.x * APPLY_TILE + threadIdx.x;
-    const bool act = t < ntarg;
-    double x0 = 0, x1 = 0, x2 = 0, m0 = 0, m1 = 0, m2 = 0;
-    int64_t self = -1;
-    if (act) {
-        x0 = txyz[3 * t]; x1 = txyz[3 * t + 1]; x2 = txyz[3 * t + 2];
-        m0 = tnrm[3 * t]; m1 = tnrm[3 * t + 1]; m2 = tnrm[3 * t + 2];
-        if (tself) self = tself[t];
-    }
-    const double inv4pi = 0.07957747154594767;
-    double acc = 0.0;
-    for (int64_t base = 0; base < nnode; base += APPLY_TILE) {
-        __syncthreads();
-        const int64_t j = base + threadIdx.x;
-        if (j < nnode) {
-            for (int a = 0; a < 3; a++) { sx[3 * threadIdx.x + a] = xyz[3 * j + a]; sn[3 * threadIdx.x + a] = nrm[3 * j + a]; }
-            sw[threadIdx.x] = wts[j] * sig[j] * inv4pi;
-        }
-        __syncthreads();
-        const int nt = (int)min((int64_t)APPLY_TILE, nnode - base);
-        if (act)
-            for (int k = 0; k < nt; k++) {
-                if (base + k == self) continue;
-                const double d0 = x0 - sx[3 * k], d1 = x1 - sx[3 * k + 1], d2 = x2 - sx[3 * k + 2];
-                const double r2 = d0 * d0 + d1 * d1 + d2 * d2, ri = rsqrt(r2), ri2 = ri * ri, ri3 = ri2 * ri;
-                double kv;
-                if (kernel == RRQ_S) kv = ri;
-                else if (kernel == RRQ_D) kv = (d0 * sn[3 * k] + d1 * sn[3 * k + 1] + d2 * sn[3 * k + 2]) * ri3;
-                else if (kernel == RRQ_SP) kv = -(d0 * m0 + d1 * m1 + d2 * m2) * ri3;
-                else {
-                    const double dn = d0 * sn[3 * k] + d1 * sn[3 * k + 1] + d2 * sn[3 * k + 2];
-                    const double dm = d0 * m0 + d1 * m1 + d2 * m2;
-                    kv = (m0 * sn[3 * k] + m1 * sn[3 * k + 1] + m2 * sn[3 * k + 2]) * ri3 - 3.0 * dn * dm * ri3 * ri2;
-                }
-                acc += kv * sw[k];
-            }
-    }
-    if (act) out[t] = acc;
+// Kernel values without the 1/(4 pi) factor: d = x_t - x_j, ri = 1/|d|, n = source
+// normal, m = target normal (Sec. 1, eqs. slpdef-dprimelpdef).
+template <int K, typename T>
+__device__ __forceinline__ T kernel_value(T d0, T d1, T d2, T ri, T n0, T n1, T n2, T m0, T m1, T m2) {
+    const T ri3 = ri * ri * ri;
+    if (K == RRQ_S) return ri;
+    if (K == RRQ_D) return (d0 * n0 + d1 * n1 + d2 * n2) * ri3;
+    if (K == RRQ_SP) return -(d0 * m0 + d1 * m1 + d2 * m2) * ri3;
+    const T dn = d0 * n0 + d1 * n1 + d2 * n2, dm = d0 * m0 + d1 * m1 + d2 * m2;
+    return (m0 * n0 + m1 * n1 + m2 * n2) * ri3 - T(3) * dn * dm * ri3 * ri * ri;
 }
-
-// Mixed-precision apply.  The smooth sum is split at the distance r_c = eta x (smallest
-// spread of the nodes of one patch): every node closer than r_c to a target belongs to
-// one of the target's near patches (|x_t - c_P| <= |x_t - x_j| + R_P <= R_P + eta d_P),
-// hence to its CSR row.  Terms with |x_t - x_j| >= r_c are summed in FP32 over all
-// sources (k_apply_f32); terms with |x_t - x_j| < r_c -- the large, ill-conditioned ones
-// that the correction cancels -- are added in FP64 by the SpMV over the row
-// (k_spmv_near64).  Both kernels decide "< r_c" by the same FP32 computation
-// (split_r2), so every source is counted exactly once.
 
 // x as a (hi, lo) FP32 pair
 __device__ __forceinline__ void split2(double x, float &h, float &l) {
@@ -874,6 +854,163 @@ __device__ __forceinline__ float split_r2(const float th[3], const float tl[3], 
                                           float d[3]) {
     for (int a = 0; a < 3; a++) d[a] = (th[a] - sh[a]) + (tl[a] - sl[a]);
     return fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+}
+
+// Sum over the CSR row of target t of val[q] sigma[col[q]] (one warp; lanes stride the
+// row, four independent loads in flight per lane), plus, when MIXED, the smooth terms of
+// the row's nodes closer than r_c in FP64 (see rrq_apply).  Returns the warp sum in
+// every lane.
+template <int K, bool MIXED>
+__device__ __forceinline__ double row_sum(int64_t a, int64_t b, const int32_t *__restrict__ col,
+                                          const double *__restrict__ val, const double *__restrict__ sig,
+                                          const double *__restrict__ xyz, const double *__restrict__ nrm,
+                                          const double *__restrict__ wts, const double x[3], const double m[3],
+                                          int64_t self, float rc2, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t q = a + lane;
+    for (; q + 96 < b; q += 128) {
+        const double v0 = __ldcs(val + q), v1 = __ldcs(val + q + 32), v2 = __ldcs(val + q + 64),
+                     v3 = __ldcs(val + q + 96);
+        const int32_t c0 = __ldcs(col + q), c1 = __ldcs(col + q + 32), c2 = __ldcs(col + q + 64),
+                      c3 = __ldcs(col + q + 96);
+        s0 = fma(v0, __ldg(sig + c0), s0);
+        s1 = fma(v1, __ldg(sig + c1), s1);
+        s2 = fma(v2, __ldg(sig + c2), s2);
+        s3 = fma(v3, __ldg(sig + c3), s3);
+    }
+    for (; q < b; q += 32) s0 = fma(__ldcs(val + q), __ldg(sig + __ldcs(col + q)), s0);
+    double s = (s0 + s1) + (s2 + s3);
+    if (MIXED) {
+        float th[3], tl[3];
+        for (int c = 0; c < 3; c++) split2(x[c], th[c], tl[c]);
+        for (int64_t r = a + lane; r < b; r += 32) {
+            const int32_t j = __ldg(col + r);
+            if (j == self) continue;
+            float sh[3], sl[3], d[3];
+            for (int c = 0; c < 3; c++) split2(__ldg(xyz + 3 * j + c), sh[c], sl[c]);
+            if (split_r2(th, tl, sh, sl, d) >= rc2) continue;
+            const double d0 = x[0] - xyz[3 * j], d1 = x[1] - xyz[3 * j + 1], d2 = x[2] - xyz[3 * j + 2];
+            const double ri = rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            const double kv = kernel_value<K, double>(d0, d1, d2, ri, nrm[3 * j], nrm[3 * j + 1], nrm[3 * j + 2], m[0],
+                                                      m[1], m[2]);
+            s = fma(kv, wts[j] * __ldg(sig + j) * kInv4Pi, s);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// One kernel per apply: the block's APPLY_TILE targets (one per thread) sum the smooth
+// rule over all nodes, staged through shared memory tile by tile (the coincident node
+// skipped); then its eight warps walk the block's CSR rows (row_sum) and every target
+// adds its row.  FP64: every term in FP64.  MIXED: terms with |x_t - x_j| >= r_c in FP32
+// (coordinates as (hi, lo) FP32 pairs, Kahan-compensated sums per source tile, FP64
+// across tiles), the closer ones -- all in the target's row -- in FP64 with the row.
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(APPLY_TILE) k_apply_fused(
+    const double *__restrict__ xyz, const double *__restrict__ nrm, const double *__restrict__ wts,
+    const double *__restrict__ sig, int64_t nnode, const double *__restrict__ txyz, const double *__restrict__ tnrm,
+    const int64_t *__restrict__ tself, int64_t ntarg, const int64_t *__restrict__ rowptr,
+    const int32_t *__restrict__ col, const double *__restrict__ val, float rc2, double *__restrict__ out) {
+    constexpr bool kNeedN = (K == RRQ_D || K == RRQ_DP);
+    typedef typename std::conditional<MIXED, float, double>::type R;
+    __shared__ R sx[APPLY_TILE * 3], sxl[MIXED ? APPLY_TILE * 3 : 1], sn[kNeedN ? APPLY_TILE * 3 : 1], sw[APPLY_TILE];
+    __shared__ double srow[APPLY_TILE];
+    const int64_t t0 = (int64_t)blockIdx.x * APPLY_TILE;
+    const int64_t t = t0 + threadIdx.x;
+    const bool act = t < ntarg;
+    double x[3] = {0, 0, 0}, m[3] = {0, 0, 0};
+    int64_t self = -1;
+    if (act) {
+        for (int a = 0; a < 3; a++) { x[a] = txyz[3 * t + a]; m[a] = tnrm[3 * t + a]; }
+        if (tself) self = tself[t];
+    }
+    float th[3], tl[3], mf[3];
+    for (int a = 0; a < 3; a++) {
+        split2(x[a], th[a], tl[a]);
+        mf[a] = __double2float_rn(m[a]);
+    }
+    double acc = 0.0;
+    for (int64_t base = 0; base < nnode; base += APPLY_TILE) {
+        __syncthreads();
+        const int64_t j = base + threadIdx.x;
+        if (j < nnode) {
+            for (int a = 0; a < 3; a++) {
+                if (MIXED) {
+                    float h, l;
+                    split2(xyz[3 * j + a], h, l);
+                    sx[3 * threadIdx.x + a] = h;
+                    sxl[3 * threadIdx.x + a] = l;
+                } else {
+                    sx[3 * threadIdx.x + a] = (R)xyz[3 * j + a];
+                }
+                if (kNeedN) sn[3 * threadIdx.x + a] = (R)nrm[3 * j + a];
+            }
+            sw[threadIdx.x] = (R)(wts[j] * sig[j] * kInv4Pi);
+        }
+        __syncthreads();
+        const int nt = (int)min((int64_t)APPLY_TILE, nnode - base);
+        if (!act) continue;
+        if (MIXED) {
+            float s = 0.0f, c = 0.0f;
+            for (int k = 0; k < nt; k++) {
+                float d[3];
+                const float r2 = split_r2(th, tl, (const float *)sx + 3 * k, (const float *)sxl + 3 * k, d);
+                const float ri = rsqrtf(r2);
+                const float n0 = kNeedN ? (float)sn[3 * k] : 0.f, n1 = kNeedN ? (float)sn[3 * k + 1] : 0.f,
+                            n2 = kNeedN ? (float)sn[3 * k + 2] : 0.f;
+                const float kv = kernel_value<K, float>(d[0], d[1], d[2], ri, n0, n1, n2, mf[0], mf[1], mf[2]);
+                const float term = r2 < rc2 ? 0.0f : kv * (float)sw[k];  // close sources: FP64 with the row
+                const float y = term - c;                               // Kahan step
+                const float tt = s + y;
+                c = (tt - s) - y;
+                s = tt;
+            }
+            acc += (double)s - (double)c;
+        } else {
+            for (int k = 0; k < nt; k++) {
+                if (base + k == self) continue;
+                const double d0 = x[0] - (double)sx[3 * k], d1 = x[1] - (double)sx[3 * k + 1],
+                             d2 = x[2] - (double)sx[3 * k + 2];
+                const double ri = rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                const double n0 = kNeedN ? (double)sn[3 * k] : 0.0, n1 = kNeedN ? (double)sn[3 * k + 1] : 0.0,
+                             n2 = kNeedN ? (double)sn[3 * k + 2] : 0.0;
+                acc = fma(kernel_value<K, double>(d0, d1, d2, ri, n0, n1, n2, m[0], m[1], m[2]), (double)sw[k], acc);
+            }
+        }
+    }
+    if (val) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int i = warp; i < APPLY_TILE; i += APPLY_TILE / 32) {
+            const int64_t r = t0 + i;
+            double v = 0.0;
+            if (r < ntarg) {
+                double xr[3] = {0, 0, 0}, mr[3] = {0, 0, 0};
+                if (MIXED)
+                    for (int a = 0; a < 3; a++) { xr[a] = txyz[3 * r + a]; mr[a] = tnrm[3 * r + a]; }
+                v = row_sum<K, MIXED>(rowptr[r], rowptr[r + 1], col, val, sig, xyz, nrm, wts, xr, mr,
+                                      (MIXED && tself) ? tself[r] : -1, rc2, lane);
+            }
+            if (lane == 0) srow[i] = v;
+        }
+        __syncthreads();
+        acc += srow[threadIdx.x];
+    }
+    if (act) out[t] = acc;
+}
+
+// out[t] = (accumulate ? out[t] : 0) + sum over row t of val[q] sigma[col[q]]: one warp
+// per row (row_sum).  HBM bound: 12 bytes per entry plus the row pointers.
+__global__ void __launch_bounds__(256) k_spmv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                             const double *__restrict__ val, const double *__restrict__ sig,
+                                             int64_t nrows, int accumulate, double *__restrict__ out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    const double none[3] = {0, 0, 0};
+    const double s = row_sum<RRQ_S, false>(rowptr[row], rowptr[row + 1], col, val, sig, nullptr, nullptr, nullptr,
+                                           none, none, -1, 0.f, lane);
+    if (lane == 0) out[row] = accumulate ? out[row] + s : s;
 }
 
 // smallest spread (largest node-to-node distance) over the patches, as ordered bits
@@ -891,124 +1028,31 @@ __global__ void k_patch_spread(const int64_t *__restrict__ node_off, int npatch,
     atomicMin(out, (unsigned long long)__double_as_longlong(sqrt(m)));
 }
 
-__global__ void __launch_bounds__(APPLY_TILE) k_apply_f32(int kernel, const double *__restrict__ xyz,
-                                                          const double *__restrict__ nrm,
-                                                          const double *__restrict__ wts, const double *__restrict__ sig,
-                                                          int64_t nnode, const double *__restrict__ txyz,
-                                                          const double *__restrict__ tnrm, int64_t ntarg, float rc2,
-                                                          double *__restrict__ out) {
-    __shared__ float sxh[APPLY_TILE * 3], sxl[APPLY_TILE * 3], sn[APPLY_TILE * 3], sw[APPLY_TILE];
-    const int64_t t = (int64_t)blockIdx.x * APPLY_TILE + threadIdx.x;
-    const bool act = t < ntarg;
-    float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0}, m[3] = {0, 0, 0};
-    if (act)
-        for (int a = 0; a < 3; a++) {
-            split2(txyz[3 * t + a], th[a], tl[a]);
-            m[a] = __double2float_rn(tnrm[3 * t + a]);
-        }
-    const double inv4pi = 0.07957747154594767;
-    double acc = 0.0;
-    for (int64_t base = 0; base < nnode; base += APPLY_TILE) {
-        __syncthreads();
-        const int64_t j = base + threadIdx.x;
-        if (j < nnode) {
-            for (int a = 0; a < 3; a++) {
-                split2(xyz[3 * j + a], sxh[3 * threadIdx.x + a], sxl[3 * threadIdx.x + a]);
-                sn[3 * threadIdx.x + a] = __double2float_rn(nrm[3 * j + a]);
-            }
-            sw[threadIdx.x] = __double2float_rn(wts[j] * sig[j] * inv4pi);
-        }
-        __syncthreads();
-        const int nt = (int)min((int64_t)APPLY_TILE, nnode - base);
-        if (act) {
-            float s = 0.0f, c = 0.0f;
-            for (int k = 0; k < nt; k++) {
-                float d[3];
-                const float r2 = split_r2(th, tl, sxh + 3 * k, sxl + 3 * k, d);
-                const float ri = rsqrtf(r2), ri2 = ri * ri, ri3 = ri2 * ri;
-                float kv;
-                if (kernel == RRQ_S) kv = ri;
-                else if (kernel == RRQ_D) kv = fmaf(d[0], sn[3 * k], fmaf(d[1], sn[3 * k + 1], d[2] * sn[3 * k + 2])) * ri3;
-                else if (kernel == RRQ_SP) kv = -fmaf(d[0], m[0], fmaf(d[1], m[1], d[2] * m[2])) * ri3;
-                else {
-                    const float dn = fmaf(d[0], sn[3 * k], fmaf(d[1], sn[3 * k + 1], d[2] * sn[3 * k + 2]));
-                    const float dm = fmaf(d[0], m[0], fmaf(d[1], m[1], d[2] * m[2]));
-                    kv = fmaf(m[0], sn[3 * k], fmaf(m[1], sn[3 * k + 1], m[2] * sn[3 * k + 2])) * ri3 - 3.0f * dn * dm * ri3 * ri2;
-                }
-                const float term = r2 < rc2 ? 0.0f : kv * sw[k];  // close sources: FP64 in the SpMV
-                // Kahan step: s + c holds the tile's sum
-                const float y = term - c;
-                const float tt = s + y;
-                c = (tt - s) - y;
-                s = tt;
-            }
-            acc += (double)s - (double)c;
-        }
+template <bool MIXED>
+cudaError_t launch_apply(int kernel, const Inputs &in, const double *sig, const rrq_csr *corr, const double *val,
+                         float rc2, double *out, cudaStream_t st) {
+    const unsigned grid = (unsigned)((in.ntarg + APPLY_TILE - 1) / APPLY_TILE);
+    const int64_t *rp = corr ? corr->rowptr : nullptr;
+    const int32_t *cl = corr ? corr->col : nullptr;
+#define RRQ_APPLY_CASE(KK)                                                                                     \
+    case KK:                                                                                                   \
+        k_apply_fused<KK, MIXED><<<grid, APPLY_TILE, 0, st>>>(in.xyz, in.nrm, in.wts, sig, in.nnode, in.txyz, \
+                                                              in.tnrm, in.tself, in.ntarg, rp, cl, val, rc2, out); \
+        break;
+    switch (kernel) {
+        RRQ_APPLY_CASE(RRQ_S)
+        RRQ_APPLY_CASE(RRQ_D)
+        RRQ_APPLY_CASE(RRQ_SP)
+        RRQ_APPLY_CASE(RRQ_DP)
+        default: return cudaErrorInvalidValue;
     }
-    if (act) out[t] = acc;
+#undef RRQ_APPLY_CASE
+    RRQ_COUNT_LAUNCH();
+    return cudaGetLastError();
 }
 
-// out[t] += sum_q val[q] sigma[col[q]] + (smooth terms of the row's nodes closer than r_c,
-// in FP64): one warp per row, as k_spmv plus a gather of the node positions
-__global__ void __launch_bounds__(256) k_spmv_near64(int kernel, const int64_t *__restrict__ rowptr,
-                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                     const double *__restrict__ sig, const double *__restrict__ xyz,
-                                                     const double *__restrict__ nrm, const double *__restrict__ wts,
-                                                     const double *__restrict__ txyz, const double *__restrict__ tnrm,
-                                                     const int64_t *__restrict__ tself, float rc2, int64_t nrows,
-                                                     double *__restrict__ out) {
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= nrows) return;
-    const int64_t a = rowptr[row], b = rowptr[row + 1];
-    const double x0 = txyz[3 * row], x1 = txyz[3 * row + 1], x2 = txyz[3 * row + 2];
-    const double m0 = tnrm[3 * row], m1 = tnrm[3 * row + 1], m2 = tnrm[3 * row + 2];
-    const int64_t self = tself ? tself[row] : -1;
-    float th[3], tl[3];
-    split2(x0, th[0], tl[0]);
-    split2(x1, th[1], tl[1]);
-    split2(x2, th[2], tl[2]);
-    const double inv4pi = 0.07957747154594767;
-    double s = 0.0;
-    for (int64_t q = a + lane; q < b; q += 32) {
-        const int32_t j = __ldcs(col + q);
-        const double sj = __ldg(sig + j);
-        s = fma(__ldcs(val + q), sj, s);
-        if (j == self) continue;
-        float sh[3], sl[3], d[3];
-        for (int c = 0; c < 3; c++) split2(__ldg(xyz + 3 * j + c), sh[c], sl[c]);
-        if (split_r2(th, tl, sh, sl, d) >= rc2) continue;
-        const double d0 = x0 - xyz[3 * j], d1 = x1 - xyz[3 * j + 1], d2 = x2 - xyz[3 * j + 2];
-        const double r2 = d0 * d0 + d1 * d1 + d2 * d2, ri = rsqrt(r2), ri2 = ri * ri, ri3 = ri2 * ri;
-        const double n0 = nrm[3 * j], n1 = nrm[3 * j + 1], n2 = nrm[3 * j + 2];
-        double kv;
-        if (kernel == RRQ_S) kv = ri;
-        else if (kernel == RRQ_D) kv = (d0 * n0 + d1 * n1 + d2 * n2) * ri3;
-        else if (kernel == RRQ_SP) kv = -(d0 * m0 + d1 * m1 + d2 * m2) * ri3;
-        else {
-            const double dn = d0 * n0 + d1 * n1 + d2 * n2, dm = d0 * m0 + d1 * m1 + d2 * m2;
-            kv = (m0 * n0 + m1 * n1 + m2 * n2) * ri3 - 3.0 * dn * dm * ri3 * ri2;
-        }
-        s = fma(kv, wts[j] * sj * inv4pi, s);
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[row] += s;
-}
-
-// out[t] += sum_q val[q] sigma[col[q]] over row t: one warp per row, lanes stride the
-// row's entries (coalesced val/col loads; sigma gathers hit L1/L2).  HBM bound: 12 bytes
-// per entry plus the row pointers.
-__global__ void __launch_bounds__(256) k_spmv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                             const double *__restrict__ val, const double *__restrict__ sig,
-                                             int64_t nrows, double *__restrict__ out) {
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= nrows) return;
-    const int64_t a = rowptr[row], b = rowptr[row + 1];
-    double s = 0.0;
-    for (int64_t q = a + lane; q < b; q += 32) s = fma(__ldcs(val + q), __ldg(sig + __ldcs(col + q)), s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[row] += s;
+int kernel_slot(int32_t kernel) {
+    return kernel == RRQ_S ? 0 : kernel == RRQ_D ? 1 : kernel == RRQ_SP ? 2 : kernel == RRQ_DP ? 3 : -1;
 }
 
 }  // namespace
@@ -1016,7 +1060,8 @@ __global__ void __launch_bounds__(256) k_spmv(const int64_t *__restrict__ rowptr
 extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq_targets *targ, int32_t kernel,
                                 const rrq_csr *corr, const double *density, double *out, const rrq_options *opt) {
     if (!ctx || !density || !out) return RRQ_ERR_ARG;
-    if (kernel != RRQ_S && kernel != RRQ_D && kernel != RRQ_SP && kernel != RRQ_DP) return RRQ_ERR_ARG;
+    const int kidx = kernel_slot(kernel);
+    if (kidx < 0) return RRQ_ERR_ARG;
     rrq_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
@@ -1027,7 +1072,6 @@ extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq
     Inputs in;
     rrq_status rs = prepare_inputs(ctx, s, surf, targ, o.inputs_on_host != 0, true, in);
     if (rs != RRQ_OK) return rs;
-    int kidx = kernel == RRQ_S ? 0 : kernel == RRQ_D ? 1 : kernel == RRQ_SP ? 2 : 3;
     const double *val = nullptr;
     if (corr) {
         if (corr->nrows != in.ntarg || !(corr->kernel_mask & (uint32_t)kernel)) return RRQ_ERR_ARG;
@@ -1051,6 +1095,7 @@ extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq
         const unsigned long long init = 0x7FF0000000000000ULL;  // +inf
         CK(cudaMemcpyAsync(red, &init, sizeof(init), cudaMemcpyHostToDevice, s.st));
         k_patch_spread<<<(unsigned)((in.npatch + 127) / 128), 128, 0, s.st>>>(in.node_off, in.npatch, in.xyz, red);
+        RRQ_COUNT_LAUNCH();
         CK(cudaGetLastError());
         unsigned long long h = 0;
         CK(cudaMemcpyAsync(&h, red, sizeof(h), cudaMemcpyDeviceToHost, s.st));
@@ -1063,22 +1108,10 @@ extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq
     if (in.ntarg > 0) {
         CK(cudaEventRecord(ctx->ev[0], s.st));
         if (mixed)
-            k_apply_f32<<<(unsigned)((in.ntarg + APPLY_TILE - 1) / APPLY_TILE), APPLY_TILE, 0, s.st>>>(
-                kernel, in.xyz, in.nrm, in.wts, d_sig, in.nnode, in.txyz, in.tnrm, in.ntarg, rc2, d_out);
+            CK(launch_apply<true>(kernel, in, d_sig, corr, val, rc2, d_out, s.st));
         else
-            k_apply<<<(unsigned)((in.ntarg + APPLY_TILE - 1) / APPLY_TILE), APPLY_TILE, 0, s.st>>>(
-                kernel, in.xyz, in.nrm, in.wts, d_sig, in.nnode, in.txyz, in.tnrm, in.tself, in.ntarg, d_out);
-        CK(cudaGetLastError());
+            CK(launch_apply<false>(kernel, in, d_sig, corr, val, rc2, d_out, s.st));
         CK(cudaEventRecord(ctx->ev[1], s.st));
-        if (mixed)
-            k_spmv_near64<<<(unsigned)((in.ntarg * 32 + 255) / 256), 256, 0, s.st>>>(
-                kernel, corr->rowptr, corr->col, val, d_sig, in.xyz, in.nrm, in.wts, in.txyz, in.tnrm, in.tself, rc2,
-                in.ntarg, d_out);
-        else if (val)
-            k_spmv<<<(unsigned)((in.ntarg * 32 + 255) / 256), 256, 0, s.st>>>(corr->rowptr, corr->col, val, d_sig,
-                                                                              in.ntarg, d_out);
-        CK(cudaGetLastError());
-        CK(cudaEventRecord(ctx->ev[2], s.st));
     }
     if (o.inputs_on_host && in.ntarg > 0)
         CK(cudaMemcpyAsync(out, d_out, sizeof(double) * in.ntarg, cudaMemcpyDeviceToHost, s.st));
@@ -1087,7 +1120,42 @@ extern "C" rrq_status rrq_apply(rrq_ctx *ctx, const rrq_surface *surf, const rrq
         float ms = 0;
         cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
         ctx->diag.ms_apply_smooth = ms;
-        cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    }
+    return RRQ_OK;
+}
+
+extern "C" rrq_status rrq_apply_correction(rrq_ctx *ctx, const rrq_csr *corr, int32_t kernel, const double *density,
+                                           int64_t nnode, double *out, int32_t accumulate, int32_t on_host) {
+    if (!ctx || !corr || !density || !out || nnode < 0) return RRQ_ERR_ARG;
+    const int kidx = kernel_slot(kernel);
+    if (kidx < 0 || !(corr->kernel_mask & (uint32_t)kernel) || !corr->val[kidx] || corr->nrows < 0) return RRQ_ERR_ARG;
+    if (corr->nrows > 0 && (!corr->rowptr || !corr->col)) return RRQ_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    Scratch s;
+    s.st = ctx->stream;
+    cudaError_t err = cudaSuccess;
+    const double *d_sig = upload(s, density, (size_t)nnode, on_host != 0, &err);
+    double *d_out = out;
+    if (on_host) {
+        d_out = (double *)Scratch::alloc(&s, sizeof(double) * (corr->nrows > 0 ? corr->nrows : 1));
+        if (d_out && accumulate && corr->nrows > 0)
+            err = cudaMemcpyAsync(d_out, out, sizeof(double) * corr->nrows, cudaMemcpyHostToDevice, s.st);
+    }
+    if (err != cudaSuccess || s.failed) return RRQ_ERR_OOM;
+    if (corr->nrows > 0) {
+        CK(cudaEventRecord(ctx->ev[0], s.st));
+        k_spmv<<<(unsigned)((corr->nrows * 32 + 255) / 256), 256, 0, s.st>>>(corr->rowptr, corr->col,
+                                                                              corr->val[kidx], d_sig, corr->nrows,
+                                                                              accumulate, d_out);
+        RRQ_COUNT_LAUNCH();
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ctx->ev[1], s.st));
+        if (on_host) CK(cudaMemcpyAsync(out, d_out, sizeof(double) * corr->nrows, cudaMemcpyDeviceToHost, s.st));
+    }
+    CK(cudaStreamSynchronize(s.st));
+    if (corr->nrows > 0) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
         ctx->diag.ms_apply_spmv = ms;
     }
     return RRQ_OK;
@@ -1264,6 +1332,7 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     pd.XSp = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X(pd.pmax));
     pd.XS2 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_X(pd.pmax));
     pd.XS1 = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_XS1(pd.pmax));
+    pd.lu = pd_lu(pd.pmax) ? (double *)StaticArena::alloc(&ar, sizeof(double) * NPc * pd_lu(pd.pmax)) : nullptr;
     pd.status = (int *)StaticArena::alloc(&ar, sizeof(int) * NPc);
     pd.kappa = (double *)StaticArena::alloc(&ar, sizeof(double) * NPc);
     int32_t *d_plists = (int32_t *)StaticArena::alloc(&ar, sizeof(int32_t) * npatch);

@@ -250,6 +250,7 @@ rrq_status create_impl(rrq_ctx *ctx, rrq_batch *b, int32_t nsurf, const rrq_surf
     pd.XSp = (double *)b->alloc(sizeof(double) * NP * pd_X(pd.pmax));
     pd.XS2 = (double *)b->alloc(sizeof(double) * NP * pd_X(pd.pmax));
     pd.XS1 = (double *)b->alloc(sizeof(double) * NP * pd_XS1(pd.pmax));
+    pd.lu = pd_lu(pd.pmax) ? (double *)b->alloc(sizeof(double) * NP * pd_lu(pd.pmax)) : nullptr;
     pd.status = (int *)b->alloc(sizeof(int) * NP);
     pd.kappa = (double *)b->alloc(sizeof(double) * NP);
     pd.col_off = b->col_off;

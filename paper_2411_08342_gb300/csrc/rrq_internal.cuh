@@ -58,6 +58,8 @@ struct OrderTables {
     double L2M[RRQ_PMAX * RRQ_PMAX];                // [n][k] coefficient of t^k in P_n(t)
     double Mmon[RRQ_NPMAX * RRQ_NPMAX];             // [ab][i] coefficient of u^a v^b in the node
                                                     // Lagrange function l_i (ab a-major, a + b < p)
+    double Cjl[(RRQ_PMAX + 1) * (RRQ_PMAX + 1)];    // [l][j] C_{j,l} = (j-2)!(l-j)!/(l-1)!, j >= 2
+    double Djl[(RRQ_PMAX + 1) * (RRQ_PMAX + 1)];    // [l][j] D_{j,l} = (j-1)!(l-j)!/l!, j >= 1
 };
 
 // Complex preimage of one (pair, edge): Re t0, Im t0, converged (0/1), singularity swap (0/1).
@@ -88,6 +90,8 @@ struct PatchData {
     float2 *XD2, *XSp2, *XS22, *XS12;  // the four fit matrices as (hi, lo) float pairs, or NULL
     int *status;     // [P] 0 ok, nonzero = singular fit / degenerate patch
     double *kappa;   // [P] 1-norm condition number of the fit matrix A (Sec. 5.1), or NULL
+    double *lu;      // [P][4*NPMAX*NPMAX] quaternion LU factor of the fit for orders above 12
+                     // (too large for shared memory there), or NULL
     double *xm;      // [P][NPMAX*3] monomial coefficients [ab][a] of the local node interpolant
     EdgeRoot *roots;  // [pair item][3 edges]: (Re t0, Im t0, converged, singularity swap)
     int8_t *uside;    // [pair item] side of the patch the target is on along e_z (+1, -1), 0 = unknown
@@ -104,6 +108,7 @@ __host__ __device__ __forceinline__ size_t pd_eyu(int pm) { return (size_t)3 * 4
 __host__ __device__ __forceinline__ size_t pd_eg(int pm) { return (size_t)3 * 2 * pm * ((pm + 1) * (pm + 2) / 2) * 3; }
 __host__ __device__ __forceinline__ size_t pd_X(int pm) { return 4 * pd_np(pm) * pd_np(pm); }
 __host__ __device__ __forceinline__ size_t pd_XS1(int pm) { return pd_np(pm) * pd_np(pm); }
+__host__ __device__ __forceinline__ size_t pd_lu(int pm) { return pm > 12 ? 4 * pd_np(pm) * pd_np(pm) : 0; }
 
 // Pair work item: target, patch, offset of the first CSR entry of the pair, and the
 // pair's index in target-major order (near-list order).

@@ -28,14 +28,36 @@ namespace rrqk {
 
 constexpr int WARPS = 4;
 
+// Per-pair shared-memory layout (in doubles).  Regions whose lifetimes do not overlap share
+// space, so that more pairs' CTAs fit on an SM:
+//   header YT, NUT, XT, NT, FR                 whole tile
+//   ST, GST, HST (target harmonic tables)     phases C/D .. L
+//   OM (Omega_0, Omega and nu' derivatives)   H .. L
+//   R: WV (premultiplied sample vectors)      H .. K, holding before H the edge
+//      coefficients EA (A .. D) and after K the nu'-derivative table DST and (mixed)
+//      the split target table STF (L0 .. L), then the row vectors B, BD, BP, PSI
+//      (L .. M) when they fit
+//   early scratch after WV: DQ, TAU, RINV, OM1, OM3, UP/MOM, T0, EM   C .. H
+//   line integrals Q, DQQ, V over the early scratch                     K .. L
+//   B, BD, BP, PSI after the line integrals when they do not fit in WV  L .. M
+// Every region starts at an even double offset and TOTAL is even, so that the (hi, lo)
+// float4 views of the mixed path are 16-byte aligned.
 template <int P>
 struct PairSm {
     static constexpr int NP = P * (P + 1) / 2, PT = 2 * P, NJK = (P + 1) * (P + 2) / 2, NS = 3 * PT, NUP = 2 * PT;
+    static constexpr int ev(int x) { return (x + 1) & ~1; }
+    static constexpr int mx(int a, int b) { return a > b ? a : b; }
     static constexpr int YT = 0, NUT = 3, XT = 6, NT = 9, FR = 12;   // FR: 16
-    static constexpr int EA = 28;                                     // 9P
-    // every region from here on starts at an even double offset and TOTAL is even, so that
-    // the (hi, lo) float4 views of the mixed path are 16-byte aligned
-    static constexpr int DQ = (EA + 9 * P + 1) & ~1;                  // NS*3
+    static constexpr int ST = 28;                                     // NJK complex
+    static constexpr int GST = ST + 2 * NJK;                          // NJK*3 complex
+    static constexpr int HST = GST + 6 * NJK;                         // NJK*6 complex
+    static constexpr int OM = HST + 12 * NJK;                         // 8
+    static constexpr int R = OM + 8;
+    static constexpr int WV = R;                                      // NS*12
+    static constexpr int EA = R;                                      // 9P
+    static constexpr int DST = R;                                     // NJK complex
+    static constexpr int STF = R + 2 * NJK;                           // NJK complex (mixed)
+    static constexpr int DQ = R + 12 * NS;                            // NS*3
     static constexpr int TAU = DQ + 3 * NS;                           // NS*3
     static constexpr int RINV = TAU + 3 * NS;                         // NS
     static constexpr int OM1 = RINV + NS;                             // NS
@@ -45,19 +67,19 @@ struct PairSm {
     static constexpr int UP = OM3 + NS;                               // 3*2*NUP
     static constexpr int MOM = UP;
     static constexpr int T0 = UP + 6 * NUP;                           // 3*4 (re, im, conv, ssq)
-    static constexpr int ST = T0 + 12;                                // NJK complex
-    static constexpr int GST = ST + 2 * NJK;                          // NJK*3 complex
-    static constexpr int HST = GST + 6 * NJK;                         // NJK*6 complex
-    static constexpr int Q = HST + 12 * NJK;                          // NJK*4 complex
+    static constexpr int EM = T0 + 12;                                // 3*P*3 monomial edge coefficients
+    static constexpr int EEND = EM + 9 * P;
+    static constexpr int Q = DQ;                                      // NJK*4 complex
     static constexpr int DQQ = Q + 8 * NJK;                           // NJK*4 complex
     static constexpr int V = DQQ + 8 * NJK;                           // NJK complex
-    static constexpr int OM = V + 2 * NJK;                            // 8
-    static constexpr int B = OM + 8;                                  // NP*4
+    static constexpr int QEND = V + 2 * NJK;
+    static constexpr bool OUT_IN_WV = 4 * NJK + 13 * NP <= 12 * NS;
+    static constexpr int B = OUT_IN_WV ? R + 4 * NJK : ev(QEND);    // NP*4
     static constexpr int BD = B + 4 * NP;                             // NP*4
-    static constexpr int PSI = BD + 4 * NP;                           // NP
-    static constexpr int WV = PSI + NP;                               // NS*12 premultiplied sample vectors
-    static constexpr int EM = WV + 12 * NS;                           // 3*P*3 monomial edge coefficients
-    static constexpr int TOTAL = (EM + 9 * P + 2 + 1) & ~1;
+    static constexpr int BP = BD + 4 * NP;                            // NP*4: (0, nu') B
+    static constexpr int PSI = BP + 4 * NP;                           // NP
+    static constexpr int TOTAL = ev(mx(mx(EEND, QEND), PSI + NP));
+    static_assert(9 * P <= 12 * NS && 4 * NJK <= 12 * NS, "region R too small");
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -81,7 +103,9 @@ __device__ __forceinline__ double rcp_small(int n) {
     constexpr double R[2 * RRQ_PMAX + 2] = {0.0,      1.0,      1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
                                             1.0 / 7,  1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13,
                                             1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20,
-                                            1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25};
+                                            1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27,
+                                            1.0 / 28, 1.0 / 29};
+    static_assert(2 * RRQ_PMAX + 2 == 30, "extend the table with the order limit");
     return R[n];
 }
 

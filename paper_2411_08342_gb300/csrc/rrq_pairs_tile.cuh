@@ -131,13 +131,6 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
     }
     if (tid < 5) bc[tid] = 0;
     const double inv4pi = 0.07957747154594767, sq2 = 1.4142135623730951;
-    constexpr double FACT[2 * RRQ_PMAX + 2] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0, 5040.0, 40320.0, 362880.0,
-                                               3628800.0, 39916800.0, 479001600.0, 6227020800.0, 87178291200.0,
-                                               1307674368000.0, 20922789888000.0, 355687428096000.0,
-                                               6402373705728000.0, 121645100408832000.0, 2432902008176640000.0,
-                                               51090942171709440000.0, 1124000727777607680000.0,
-                                               25852016738884976640000.0, 620448401733239439360000.0,
-                                               15511210043330985984000000.0};
 #define SW(pl) (smraw + (size_t)(pl) * Z::TOTAL)
     // tiles of T consecutive items: grid-stride, or (persistent launch) fetched from a counter
     for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
@@ -638,8 +631,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
         }
         __syncthreads();
         // L0: nu' derivative of the target harmonics, dS^{(n,q)} = grad S^{(n,q)}(y') . nu', per
-        // (pair, (n, q >= 0)), into the singularity-swap scratch (dead after phase G2)
-        // (mixed: the target harmonics as double-float pairs too, into the tangent scratch)
+        // (pair, (n, q >= 0)), into the per-sample vectors' space (dead after phase K)
+        // (mixed: the target harmonics as double-float pairs too, beside it)
         if (wantDP || MIX) {
             for (int f = tid; f < nt * NJK; f += nth) {
                 const int pl = f / NJK, jk = f % NJK;
@@ -649,10 +642,10 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const cd dS = mkc(fma(gg[0].x, nut[0], fma(gg[1].x, nut[1], gg[2].x * nut[2])),
                                   fma(gg[0].y, nut[0], fma(gg[1].y, nut[1], gg[2].y * nut[2])));
                 if (MIX) {
-                    reinterpret_cast<float4 *>(sw + Z::UP)[jk] = split4c(dS);
-                    reinterpret_cast<float4 *>(sw + Z::TAU)[jk] = split4c(reinterpret_cast<const cd *>(sw + Z::ST)[jk]);
+                    reinterpret_cast<float4 *>(sw + Z::DST)[jk] = split4c(dS);
+                    reinterpret_cast<float4 *>(sw + Z::STF)[jk] = split4c(reinterpret_cast<const cd *>(sw + Z::ST)[jk]);
                 } else {
-                    reinterpret_cast<cd *>(sw + Z::UP)[jk] = dS;
+                    reinterpret_cast<cd *>(sw + Z::DST)[jk] = dS;
                 }
             }
             __syncthreads();
@@ -667,15 +660,15 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const cd *St = reinterpret_cast<const cd *>(sw + Z::ST), *gSt = reinterpret_cast<const cd *>(sw + Z::GST);
             const cd *HSt = reinterpret_cast<const cd *>(sw + Z::HST), *Qs = reinterpret_cast<const cd *>(sw + Z::Q);
             const cd *dQs = reinterpret_cast<const cd *>(sw + Z::DQQ), *Vs = reinterpret_cast<const cd *>(sw + Z::V);
-            const cd *dSt = reinterpret_cast<const cd *>(sw + Z::UP);
+            const cd *dSt = reinterpret_cast<const cd *>(sw + Z::DST);
             int l = 1;
             while ((l + 1) * l / 2 <= lm) l++;
             const int m = lm - l * (l - 1) / 2 + 1;
             double Ib0 = 0, Ib1 = 0, Ib2 = 0, Ib3 = 0, Ip = 0, dI0 = 0, dI1 = 0, dI2 = 0, dI3 = 0;
             if (MIX) {
                 // the same sums in double-float on the FP32 pipes; each j's sums in FP64 after
-                const float4 *Stf = reinterpret_cast<const float4 *>(sw + Z::TAU);
-                const float4 *dStf = reinterpret_cast<const float4 *>(sw + Z::UP);
+                const float4 *Stf = reinterpret_cast<const float4 *>(sw + Z::STF);
+                const float4 *dStf = reinterpret_cast<const float4 *>(sw + Z::DST);
                 const float4 *Qf = reinterpret_cast<const float4 *>(sw + Z::Q);
                 const float4 *dQf = reinterpret_cast<const float4 *>(sw + Z::DQQ);
                 const float4 *Vf = reinterpret_cast<const float4 *>(sw + Z::V);
@@ -701,9 +694,9 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                             }
                         }
                     }
-                    Ip = fma(FACT[j - 1] * FACT[l - j] / FACT[l], dfval(ip), Ip);
+                    Ip = fma(tab->Djl[l * (RRQ_PMAX + 1) + j], dfval(ip), Ip);
                     if (j >= 2) {
-                        const double Cj = FACT[j - 2] * FACT[l - j] / FACT[l - 1];
+                        const double Cj = tab->Cjl[l * (RRQ_PMAX + 1) + j];
                         Ib0 = fma(Cj, dfval(b0), Ib0); Ib1 = fma(Cj, dfval(b1), Ib1);
                         Ib2 = fma(Cj, dfval(b2), Ib2); Ib3 = fma(Cj, dfval(b3), Ib3);
                         if (wantDP) {
@@ -714,7 +707,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 }
             } else
             for (int j = 1; j <= l; j++) {
-                const double Dj = FACT[j - 1] * FACT[l - j] / FACT[l];
+                const double Dj = tab->Djl[l * (RRQ_PMAX + 1) + j];
                 const int kmin = max(-j, m - (l - j)), kmax = min(j, m + (l - j));
                 double ip = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0, e0s = 0, e1s = 0, e2s = 0, e3s = 0;
                 for (int k = kmin; k <= kmax; k++) {
@@ -743,7 +736,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 }
                 Ip = fma(Dj, ip, Ip);
                 if (j >= 2) {
-                    const double Cj = FACT[j - 2] * FACT[l - j] / FACT[l - 1];
+                    const double Cj = tab->Cjl[l * (RRQ_PMAX + 1) + j];
                     Ib0 = fma(Cj, b0, Ib0); Ib1 = fma(Cj, b1, Ib1); Ib2 = fma(Cj, b2, Ib2); Ib3 = fma(Cj, b3, Ib3);
                     if (wantDP) {
                         dI0 = fma(Cj, e0s, dI0); dI1 = fma(Cj, e1s, dI1); dI2 = fma(Cj, e2s, dI2); dI3 = fma(Cj, e3s, dI3);
@@ -766,13 +759,13 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             const double psi = fct * (Ip + St[jk_index(l, m)].y * Om[0]);
             if (MIX) {
                 // rows in double-float: the row phase reads (hi, lo) pairs in the same slots
-                float2 *Bf = reinterpret_cast<float2 *>(Bs) + 4 * lm, *Bpf = reinterpret_cast<float2 *>(sw + Z::DQ) + 4 * lm;
+                float2 *Bf = reinterpret_cast<float2 *>(Bs) + 4 * lm, *Bpf = reinterpret_cast<float2 *>(sw + Z::BP) + 4 * lm;
                 Bf[0] = split2d(B0); Bf[1] = split2d(B1); Bf[2] = split2d(B2); Bf[3] = split2d(B3);
                 Bpf[0] = split2d(Bp0); Bpf[1] = split2d(Bp1); Bpf[2] = split2d(Bp2); Bpf[3] = split2d(Bp3);
                 reinterpret_cast<float2 *>(sw + Z::PSI)[lm] = split2d(psi);
             } else {
                 Bs[4 * lm] = B0; Bs[4 * lm + 1] = B1; Bs[4 * lm + 2] = B2; Bs[4 * lm + 3] = B3;
-                double *Bp = sw + Z::DQ + 4 * lm;
+                double *Bp = sw + Z::BP + 4 * lm;
                 Bp[0] = Bp0; Bp[1] = Bp1; Bp[2] = Bp2; Bp[3] = Bp3;
                 sw[Z::PSI + lm] = psi;
             }
@@ -811,7 +804,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const PairItem im = s_item[pl];
                 const double *c = a.coef + (size_t)im.P * (13 * RRQ_NPMAX);
                 const double *cD = c, *cSp = c + 4 * RRQ_NPMAX, *cS2 = c + 8 * RRQ_NPMAX, *cS1 = c + 12 * RRQ_NPMAX;
-                const double *Bs = sw + Z::B, *Bds = sw + Z::BD, *Bp = sw + Z::DQ, *Psis = sw + Z::PSI;
+                const double *Bs = sw + Z::B, *Bds = sw + Z::BD, *Bp = sw + Z::BP, *Psis = sw + Z::PSI;
                 double qD = 0, qDp = 0, qSp = 0, qS = 0;
                 for (int lm = lane; lm < NP; lm += 32) {
                     const double B0 = Bs[4 * lm], B1 = Bs[4 * lm + 1], B2 = Bs[4 * lm + 2], B3 = Bs[4 * lm + 3];
@@ -836,14 +829,14 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                         const double *xs = xyz + 3 * (o + i), *ns = nrm + 3 * (o + i);
                         const double d0 = sw[Z::XT] - xs[0], d1 = sw[Z::XT + 1] - xs[1], d2 = sw[Z::XT + 2] - xs[2];
                         const double gn0 = sw[Z::NT], gn1 = sw[Z::NT + 1], gn2 = sw[Z::NT + 2];
-                        const double r2 = d0 * d0 + d1 * d1 + d2 * d2, r = sqrt(r2), r3 = r2 * r;
+                        const double ri = rsqrt(d0 * d0 + d1 * d1 + d2 * d2), ri2 = ri * ri, ri3 = ri2 * ri;
                         const double wk = wts[o + i] * inv4pi * sg;
                         const double dns = d0 * ns[0] + d1 * ns[1] + d2 * ns[2];
                         const double dnt = d0 * gn0 + d1 * gn1 + d2 * gn2;
-                        mS -= wk / r;
-                        mD -= wk * dns / r3;
-                        mSp += wk * dnt / r3;
-                        mDp -= wk * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) / r3 - 3.0 * dns * dnt / (r3 * r2));
+                        mS -= wk * ri;
+                        mD -= wk * dns * ri3;
+                        mSp += wk * dnt * ri3;
+                        mDp -= wk * ri3 * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) - 3.0 * dns * dnt * ri2);
                     }
                 }
                 qD = warp_sum(qD); qDp = warp_sum(qDp); qSp = warp_sum(qSp); qS = warp_sum(qS);
@@ -888,7 +881,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     r0 = dfval(a0);
                     r1 = dfval(a1) * sc;
                 } else if (grp == 1) {
-                    const float2 *X = pd.XSp2 + ps * pd_X(pd.pmax), *Bpf = reinterpret_cast<const float2 *>(sw + Z::DQ);
+                    const float2 *X = pd.XSp2 + ps * pd_X(pd.pmax), *Bpf = reinterpret_cast<const float2 *>(sw + Z::BP);
                     for (int lm = 0; lm < NP; lm++)
                         for (int c = 0; c < 4; c++) {
                             const float2 x = X[(c * NP + lm) * NP + i], b = Bpf[4 * lm + c];
@@ -920,7 +913,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 }
                 r1 *= sc;
             } else if (grp == 1) {
-                const double *X = pd.XSp + ps * pd_X(pd.pmax), *Bp = sw + Z::DQ;
+                const double *X = pd.XSp + ps * pd_X(pd.pmax), *Bp = sw + Z::BP;
                 for (int lm = 0; lm < NP; lm++)
                     r0 += Bp[4 * lm] * X[(0 * NP + lm) * NP + i] + Bp[4 * lm + 1] * X[(1 * NP + lm) * NP + i] +
                           Bp[4 * lm + 2] * X[(2 * NP + lm) * NP + i] + Bp[4 * lm + 3] * X[(3 * NP + lm) * NP + i];
@@ -942,17 +935,17 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const double *xs = xyz + 3 * (o + i), *ns = nrm + 3 * (o + i);
                 const double d0 = sw[Z::XT] - xs[0], d1 = sw[Z::XT + 1] - xs[1], d2 = sw[Z::XT + 2] - xs[2];
                 const double gn0 = sw[Z::NT], gn1 = sw[Z::NT + 1], gn2 = sw[Z::NT + 2];
-                const double r2 = d0 * d0 + d1 * d1 + d2 * d2, r = sqrt(r2), r3 = r2 * r;
+                const double ri = rsqrt(d0 * d0 + d1 * d1 + d2 * d2), ri2 = ri * ri, ri3 = ri2 * ri;
                 const double wk = wts[o + i] * inv4pi;
                 const double dns = d0 * ns[0] + d1 * ns[1] + d2 * ns[2];
                 const double dnt = d0 * gn0 + d1 * gn1 + d2 * gn2;
                 if (grp == 0) {
-                    r0 -= wk * dns / r3;
-                    r1 -= wk * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) / r3 - 3.0 * dns * dnt / (r3 * r2));
+                    r0 -= wk * dns * ri3;
+                    r1 -= wk * ri3 * ((gn0 * ns[0] + gn1 * ns[1] + gn2 * ns[2]) - 3.0 * dns * dnt * ri2);
                 } else if (grp == 1) {
-                    r0 += wk * dnt / r3;
+                    r0 += wk * dnt * ri3;
                 } else {
-                    r0 -= wk / r;
+                    r0 -= wk * ri;
                 }
             }
             if (grp == s_grp[0]) col[dst] = (int32_t)(col_off[im.P] + i);

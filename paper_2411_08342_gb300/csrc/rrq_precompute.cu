@@ -128,9 +128,12 @@ struct PreSizes {
     static constexpr int HN_OFF = ASI_OFF + NP * NP;         // NP*NP
     static constexpr int TMP_OFF = HN_OFF + NP * NP;         // NP*NP
     static constexpr int TAB_OFF = TMP_OFF + NP * NP;        // NP*NJK complex (node tables)
-    // orders above 8: only the quaternion factor of the fit matrix stays in shared memory
+    // orders above 8: only the quaternion factor of the fit matrix stays in shared memory;
+    // above 12 it is kept in global memory (PatchData::lu) and shared memory holds the
+    // scalar system only
     static constexpr bool BIGP = P > 8;
-    static constexpr int PHASEB = BIGP ? 4 * NP * NP : TAB_OFF + 2 * NP * NJK;
+    static constexpr bool GLU = P > 12;
+    static constexpr int PHASEB = GLU ? NP * NP : BIGP ? 4 * NP * NP : TAB_OFF + 2 * NP * NJK;
     static constexpr int PHASEA = 2 * 3 * PT * NJK;          // edge tables
     static constexpr int BIG = PHASEB > PHASEA ? PHASEB : PHASEA;
     // persistent small arrays
@@ -156,6 +159,8 @@ __device__ __forceinline__ void lm_of(int lm, int &l, int &m) {
 
 // Steps 1-2 for orders above 8, where the 4 n_p x 4 n_p system no longer fits in shared memory
 // beside its right-hand sides: the quaternion matrix is factored in place in shared memory
+// (above order 12, where the factor alone exceeds shared memory, in the patch's slice of
+// PatchData::lu, which stays in L2 while the CTA works on it)
 // (P A = L U, pivoting on the quaternion modulus, multipliers kept below the diagonal), and
 // each right-hand side is solved by one thread with its work vector in the output array
 // itself (X_D, X_S' in global memory, element (comp, row) of column c at
@@ -168,7 +173,8 @@ __device__ void fit_big(double *sm, const double *syn, const double *snl, const 
                         int nth, int &s_bad) {
     constexpr int NP = P * (P + 1) / 2, NJK = (P + 1) * (P + 2) / 2;
     const double sq2 = 1.4142135623730951;
-    q4 *Mq = reinterpret_cast<q4 *>(sm);  // [NP][NP]
+    q4 *Mq = PreSizes<P>::GLU ? reinterpret_cast<q4 *>(pd.lu + (size_t)pid * pd_lu(pd.pmax))
+                              : reinterpret_cast<q4 *>(sm);  // [NP][NP]
     __shared__ int s_pv[NP];
     __shared__ double s_red[NP];
     __shared__ double s_anorm;
@@ -804,6 +810,8 @@ cudaError_t rrq_launch_precompute(int p, const OrderTables *d_tab, const int32_t
         case 10: return launch_pre<10>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
         case 11: return launch_pre<11>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
         case 12: return launch_pre<12>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
+        case 13: return launch_pre<13>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
+        case 14: return launch_pre<14>(d_tab, d_plist, n, d_node_off, d_xyz, d_nrm, pd, st);
         default: return cudaErrorInvalidValue;
     }
 }

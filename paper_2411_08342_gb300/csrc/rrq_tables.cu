@@ -197,6 +197,19 @@ int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, Orde
         legendre_vals(p, T->tu[s], P, dP);
         for (int n = 0; n < p; n++) T->LegU[s * p + n] = P[n];
     }
+    // the factors of the translated line integrals: C_{j,l} = int_0^1 t^{j-2} (1-t)^{l-j} dt
+    // (Thm. dlp1form) and D_{j,l} = int_0^1 t^{j-1} (1-t)^{l-j} dt (Thm. cslp1form)
+    {
+        double f[2 * RRQ_PMAX + 2];
+        f[0] = 1.0;
+        for (int n = 1; n < 2 * RRQ_PMAX + 2; n++) f[n] = f[n - 1] * n;
+        for (int l = 0; l <= RRQ_PMAX; l++)
+            for (int j = 0; j <= RRQ_PMAX; j++) {
+                const bool in = j >= 1 && j <= l;
+                T->Djl[l * (RRQ_PMAX + 1) + j] = in ? f[j - 1] * f[l - j] / f[l] : 0.0;
+                T->Cjl[l * (RRQ_PMAX + 1) + j] = (in && j >= 2) ? f[j - 2] * f[l - j] / f[l - 1] : 0.0;
+            }
+    }
     // monomial coefficients of P_n by (n+1) P_{n+1} = (2n+1) t P_n - n P_{n-1}
     for (int i = 0; i < p * p; i++) T->L2M[i] = 0.0;
     T->L2M[0] = 1.0;

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-PMAX = 12
+PMAX = 14
 S, D, SP, DP = 1, 2, 4, 8
 KERNEL_BITS = {"S": S, "D": D, "SP": SP, "DP": DP}
 KERNEL_SLOT = {"S": 0, "D": 1, "SP": 2, "DP": 3}
@@ -87,6 +87,8 @@ def load(build_if_needed: bool = True):
             L.rrq_csr_free.argtypes = [C.c_void_p, C.POINTER(CSR)]
             L.rrq_apply.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS), C.c_int32, C.POINTER(CSR),
                                     C.c_void_p, C.c_void_p, C.POINTER(Options)]
+            L.rrq_apply_correction.argtypes = [C.c_void_p, C.POINTER(CSR), C.c_int32, C.c_void_p, C.c_int64,
+                                               C.c_void_p, C.c_int32, C.c_int32]
             L.rrq_last_diagnostics.argtypes = [C.c_void_p, C.POINTER(Diag)]
             L.rrq_measure_fma_peak.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]
             L.rrq_build_corrections_static.argtypes = [C.c_void_p, C.POINTER(Surface), C.POINTER(TargetsS),
@@ -378,6 +380,16 @@ class Context:
         _check(self.L.rrq_apply(self.h, C.byref(surf), C.byref(targ), KERNEL_BITS[kernel],
                                 C.byref(csr) if csr is not None else None, _ptr(density), _ptr(out),
                                 C.byref(opt)), "rrq_apply")
+        return out
+
+    def apply_correction(self, csr: CSR, kernel: str, density, out, accumulate: bool = False,
+                         on_host: bool = False):
+        """out = (out if accumulate else 0) + C sigma for the correction CSR of `kernel`
+        (rrq_apply_correction); density and out are torch CUDA tensors, or numpy arrays
+        with on_host."""
+        n = int(density.numel()) if hasattr(density, "numel") else int(np.asarray(density).size)
+        _check(self.L.rrq_apply_correction(self.h, C.byref(csr), KERNEL_BITS[kernel], _ptr(density), n, _ptr(out),
+                                           int(accumulate), int(on_host)), "rrq_apply_correction")
         return out
 
     def fma_peak_tflops(self, fp32: bool = False) -> float:

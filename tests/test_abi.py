@@ -51,10 +51,10 @@ def test_ref_nodes_host_function():
     import numpy as np
     import pytest
     from paper_2411_08342_gb300 import rrq, workloads as W
-    for p in range(2, 13):
+    for p in range(2, rrq.PMAX + 1):
         uv, w = rrq.ref_nodes(p)
         assert np.abs(uv - W.ref_nodes(p)).max() < 1e-15, p
         assert np.abs(w - W.ref_weights(p)).max() < 1e-14, p
         assert abs(w.sum() - 0.5) < 1e-15 and abs(w @ uv[:, 0] - 1 / 6) < 1e-15, p
     with pytest.raises(rrq.RRQError, match="invalid argument"):
-        rrq.ref_nodes(13)
+        rrq.ref_nodes(rrq.PMAX + 1)

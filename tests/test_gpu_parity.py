@@ -123,7 +123,7 @@ def test_bad_arguments(ctx):
     from paper_2411_08342_gb300 import rrq
     d, tg = W.sphere80(4)
     bad = d.order.copy()
-    bad[3] = 13   # above the largest supported order
+    bad[3] = 15   # above the largest supported order
     arrs = {k: np.ascontiguousarray(v) for k, v in dict(node_off=d.node_off, xyz=d.xyz, nrm=d.nrm, wts=d.wts).items()}
     surf = ctx.surface(bad, arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
     targ = ctx.targets(np.ascontiguousarray(tg.xyz), np.ascontiguousarray(tg.nrm), np.ascontiguousarray(tg.self_node))
@@ -185,6 +185,52 @@ def test_full_size_ellipsoid_sampled(ctx, oracle_lib):
     tsel = np.sort(rng.choice(tg.n, 100, replace=False))
     errs, diag = _compare(ctx, oracle_lib, d, tg, tsel, sampled=True, label="ellipsoid 81920 p=6")
     assert diag["npairs"] > 20_000_000
+
+
+@pytest.mark.parametrize("on_host", [False, True])
+def test_apply_correction(ctx, oracle_lib, on_host):
+    """rrq_apply_correction: C sigma alone (and accumulated onto out), against numpy on the
+    CUDA CSR (the same sums, other order) and on the binary128 oracle's CSR."""
+    import torch
+    from paper_2411_08342_gb300 import rrq
+    from tests.gpu_helpers import truth_csr_rows
+    d, tg = W.star1280(6, 1500, seed=41)
+    sig = W.random_ylm_density(d.xyz, 6, seed=9)
+    arrs = rrq.device_inputs(d, tg)
+    surf = ctx.surface(arrs["order"], arrs["node_off"], arrs["xyz"], arrs["nrm"], arrs["wts"], d.ref_uv)
+    targ = ctx.targets(arrs["txyz"], arrs["tnrm"], arrs["tself"])
+    csr = ctx.build_corrections(surf, targ)
+    rowptr, col, vals = ctx.csr_to_host(csr)
+    nnz = int(rowptr[-1])
+    sel = np.arange(0, tg.n, 5)
+    trp, tcol, tvals = truth_csr_rows(oracle_lib, d, tg, sel)
+    try:
+        for k in KINDS:
+            base = np.random.default_rng(3).standard_normal(tg.n)
+            if on_host:
+                out = base.copy()
+                ctx.apply_correction(csr, k, np.ascontiguousarray(sig), out, accumulate=True, on_host=True)
+                got = out - base
+            else:
+                out = torch.as_tensor(base, device="cuda")
+                ctx.apply_correction(csr, k, torch.as_tensor(sig, device="cuda"), out, accumulate=True)
+                got = out.cpu().numpy() - base
+                out0 = torch.full((tg.n,), 7.0, dtype=torch.float64, device="cuda")
+                ctx.apply_correction(csr, k, torch.as_tensor(sig, device="cuda"), out0)
+                assert np.allclose(out0.cpu().numpy(), got, rtol=0, atol=1e-12 * np.abs(got).max())
+            v = vals[k][:nnz]
+            ref = np.zeros(tg.n)
+            nz = np.diff(rowptr) > 0
+            ref[nz] = np.add.reduceat(v * sig[col[:nnz]], rowptr[:-1][nz])
+            scale = np.zeros(tg.n)
+            scale[nz] = np.add.reduceat(np.abs(v * sig[col[:nnz]]), rowptr[:-1][nz])
+            assert np.max(np.abs(got - ref) - 1e-12 * scale - 1e-12 * np.abs(base)) <= 0, k
+            tref = np.add.reduceat(tvals[k] * sig[tcol], trp[:-1])
+            tsc = np.add.reduceat(np.abs(tvals[k] * sig[tcol]), trp[:-1])
+            print(k, "C sigma vs binary128 rows", f"{np.max(np.abs(got[sel] - tref) / tsc):.1e}")
+            assert np.max(np.abs(got[sel] - tref) / tsc) <= 1e-7, k
+    finally:
+        ctx.csr_free(csr)
 
 
 def test_apply_matches_reference(ctx, oracle_lib):
