@@ -642,7 +642,7 @@ def bench_reference(args):
     from oracle import oracle as O
     d, tg = workload()
     osf = O.OracleSurface(d)
-    n = args.cpu_targets
+    n = args.ref_targets
     times, entries = [], 0.0
     for it in range(args.warmup + args.steps):
         sel = np.arange(it * n, (it + 1) * n) % tg.n
@@ -672,7 +672,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-targets", type=int, default=20000)
+    ap.add_argument("--cpu-targets", type=int, default=20000, help="targets of the CPU-baseline sample")
+    ap.add_argument("--ref-targets", type=int, default=8000,
+                    help="targets per step of the reference arm (the oracle on the host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-apply", action="store_true", help="skip the apply, SpMV and evaluation timings")

@@ -52,7 +52,7 @@ def _rank_main(rank: int, world: int, port: int, outdir: str):
     dist.all_gather_object(gathered, (lo, hi, rp, col, vals))
     # the reference arm: only rank 0 works and prints; the others return at once
     class A:
-        steps, warmup, cpu_targets = 1, 0, 4
+        steps, warmup, cpu_targets, ref_targets = 1, 0, 4, 4
     ref_ran = False
     if rank != 0:
         bench.bench_reference(A())
