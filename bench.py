@@ -47,7 +47,9 @@ SEED = 20241115
 # DRAM bytes per (target, patch) pair of the FP64 per-pair kernel at p = 6, from a one-pass
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the launch / its pairs),
 # valid only for the kernel sources whose hash is given; otherwise reported as null.
-TRAFFIC_CAPTURE = {"sources_sha16": None, "bytes_per_pair": None, "capture": None}
+TRAFFIC_CAPTURE = {"sources_sha16": "df1fbc8cf4ecbaf9", "bytes_per_pair": 1663.0,
+                   "capture": "ncu --set full, k_pairs_tile<6, false, 5> on the 5,120-patch ellipsoid "
+                              "(4,347,204 pairs, 7.229 GB), scaled by pairs"}
 
 
 def workload(levels: int = 6):
@@ -459,7 +461,8 @@ def stellarator_leg(ctx, dev) -> dict:
     targets) at p = 4 ... 14: points per second of an S-only and a D-only correction build
     (N / T with N the number of nodes, the measure of the paper's throughput table; one
     GB300 here, one CPU core there), and the relative max error of Green's identity
-    1/2 u = S[du/dn] - D[u] for u = 1/|x| through rrq_apply with those two builds."""
+    1/2 u = S[du/dn] - D[u] for u = 1/|x| through rrq_apply with those two builds, and
+    through the density-given evaluation (rrq_evaluate_near) with the smooth rule."""
     import torch
     from paper_2411_08342_gb300 import rrq
     from paper_2411_08342_gb300 import workloads as W
@@ -490,6 +493,17 @@ def stellarator_leg(ctx, dev) -> dict:
             ctx.csr_free(csr)
             res[k] = o.cpu().numpy()
         row["green_identity_rel_err"] = float(np.abs(res["S"] - res["D"] - 0.5 * u).max() / u.max())
+        # the same identity with the corrections applied by the density-given evaluation
+        # (no matrix: the fit of the density itself), the smooth rule by rrq_apply
+        dg = {}
+        for k, dens in (("S", dudn), ("D", u)):
+            sd = torch.as_tensor(dens, device=dev)
+            sm = torch.empty(tg.n, dtype=torch.float64, device=dev)
+            ctx.apply(surf, targ, k, None, sd, sm)
+            corr = {k: torch.zeros(tg.n, dtype=torch.float64, device=dev)}
+            ctx.evaluate_near(surf, targ, sd, corr)
+            dg[k] = (sm + corr[k]).cpu().numpy()
+        row["green_identity_rel_err_density_given"] = float(np.abs(dg["S"] - dg["D"] - 0.5 * u).max() / u.max())
         out[f"p{p}"] = row
     return out
 

@@ -34,8 +34,10 @@ def _targets(d, n_on, n_off, seed):
 
 @pytest.mark.parametrize("p", [9, 10, 11, 12, 13, 14])
 def test_high_orders_on_and_off_surface(ctx, oracle_lib, p):
-    """Star surface, 80 patches: 200 on-surface nodes and 200 targets at 10^-k h."""
-    d = W.discretize(W.star_surface(1), p)
+    """Star surface, 80 patches up to p = 12 and 320 patches at p = 13, 14 (on 80 patches
+    the fit's condition number there exceeds 1e10 and binary64 rows of either
+    implementation keep only 2-3 digits): 200 on-surface nodes and 200 targets at 10^-k h."""
+    d = W.discretize(W.star_surface(1 if p <= 12 else 2), p)
     tg = _targets(d, 200, 200, seed=100 + p)
     errs, diag = compare_with_oracle(ctx, oracle_lib, d, tg, truth_max=160, label=f"p={p}")
     assert diag["npairs"] > 0
