@@ -32,9 +32,12 @@
  *   - the S^{(l,m)}(r') omega_0 term of Thm. cslp1form carries 1/(4 pi).
  *   - frame: origin = vertex mean, e_z = unit((V1-V0)x(V2-V0)), e_x along the
  *     longest edge (first of E0,E1,E2 on ties), scale 1/longest edge.
- *   - u: +e_z for a target that is a node of the patch; otherwise whichever of
- *     +e_z, -e_z maximises the minimum of u.(r'-r)/|r'-r| over the nodes and edge
- *     samples.
+ *   - u: +e_z for a target that is a node of the patch; otherwise, if the target's
+ *     footprint along e_z (the point of the node interpolant with the target's in-plane
+ *     frame coordinates) lies in the patch, the +-e_z pointing from that point to the
+ *     target; otherwise whichever of +e_z, -e_z maximises the minimum of
+ *     u.(r'-r)/|r'-r| over the nodes and edge samples (so that the half-line from the
+ *     target along u misses the patch, as Thm. dlp1form requires).
  *   - Omega_0 sign: Thm. dlp1form needs (1/4pi) d omega_0 = -grad_r G . nu da, but the
  *     printed omega_0 (eq. omega0def) integrates to +4 pi int grad_r G . nu da (checked
  *     on a disc by hand), so Omega_0 = - (line integral of the printed omega_0); its
