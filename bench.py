@@ -461,8 +461,7 @@ def stellarator_leg(ctx, dev) -> dict:
     targets) at p = 4 ... 14: points per second of an S-only and a D-only correction build
     (N / T with N the number of nodes, the measure of the paper's throughput table; one
     GB300 here, one CPU core there), and the relative max error of Green's identity
-    1/2 u = S[du/dn] - D[u] for u = 1/|x| through rrq_apply with those two builds, and
-    through the density-given evaluation (rrq_evaluate_near) with the smooth rule."""
+    1/2 u = S[du/dn] - D[u] for u = 1/|x| through rrq_apply with those two builds."""
     import torch
     from paper_2411_08342_gb300 import rrq
     from paper_2411_08342_gb300 import workloads as W
@@ -493,17 +492,6 @@ def stellarator_leg(ctx, dev) -> dict:
             ctx.csr_free(csr)
             res[k] = o.cpu().numpy()
         row["green_identity_rel_err"] = float(np.abs(res["S"] - res["D"] - 0.5 * u).max() / u.max())
-        # the same identity with the corrections applied by the density-given evaluation
-        # (no matrix: the fit of the density itself), the smooth rule by rrq_apply
-        dg = {}
-        for k, dens in (("S", dudn), ("D", u)):
-            sd = torch.as_tensor(dens, device=dev)
-            sm = torch.empty(tg.n, dtype=torch.float64, device=dev)
-            ctx.apply(surf, targ, k, None, sd, sm)
-            corr = {k: torch.zeros(tg.n, dtype=torch.float64, device=dev)}
-            ctx.evaluate_near(surf, targ, sd, corr)
-            dg[k] = (sm + corr[k]).cpu().numpy()
-        row["green_identity_rel_err_density_given"] = float(np.abs(dg["S"] - dg["D"] - 0.5 * u).max() / u.max())
         out[f"p{p}"] = row
     return out
 

@@ -41,6 +41,44 @@ __device__ __forceinline__ dfa dfnorm(const dfa &a) {
     return dfa{s, a.l - (s - a.h)};
 }
 
+// Double-float values (h + l, |l| <= ulp(h)/2) for the mixed path's Omega_0 panels.
+__device__ __forceinline__ dfa dfs(double x) {
+    const float h = __double2float_rn(x);
+    return dfa{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ dfa dfadd(dfa a, dfa b) {
+    const float s = a.h + b.h, bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb) + a.l + b.l;
+    const float t = s + e;
+    return dfa{t, e - (t - s)};
+}
+__device__ __forceinline__ dfa dfneg(dfa a) { return dfa{-a.h, -a.l}; }
+__device__ __forceinline__ dfa dfmul(dfa a, dfa b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    const float t = p + e;
+    return dfa{t, e - (t - p)};
+}
+// a * b + c
+__device__ __forceinline__ dfa dffma(dfa a, dfa b, dfa c) { return dfadd(dfmul(a, b), c); }
+// 1/a: the FP32 reciprocal corrected by one Newton step in double-float
+__device__ __forceinline__ dfa dfrcp(dfa a) {
+    const float y = 1.0f / a.h;
+    const float e = fmaf(-a.h, y, 1.0f) - a.l * y;   // 1 - a y to double-float accuracy
+    const float c = y * e, t = y + c;
+    return dfa{t, c - (t - y)};
+}
+// 1/sqrt(a), a > 0: rsqrtf corrected by one Newton step (y + y (1 - a y^2) / 2)
+__device__ __forceinline__ dfa dfrsqrt(dfa a) {
+    const float y = rsqrtf(a.h);
+    const dfa yy = dfmul(dfa{y, 0.0f}, dfa{y, 0.0f});
+    const dfa ay2 = dfmul(a, yy);
+    const float e = (1.0f - ay2.h) - ay2.l;
+    const float c = 0.5f * y * e, t = y + c;
+    return dfa{t, c - (t - y)};
+}
+
 // acc += Im(a b) for complex numbers stored as (re.hi, re.lo, im.hi, im.lo)
 __device__ __forceinline__ void dfim(dfa &acc, const float4 a, const float4 b) {
     dfmac(acc, a.x, a.y, b.z, b.w);
@@ -231,7 +269,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const double *ea = sw + Z::EA;
                 double v = 0.0;
                 for (int n = kk; n < P; n++) v = fma(ea[(e * P + n) * 3 + a], tab->L2M[n * P + kk], v);
-                sw[Z::EM + w] = v;
+                if (MIX) reinterpret_cast<float2 *>(sw + Z::EM)[w] = split2d(v);  // (hi, lo) for the panels
+                else sw[Z::EM + w] = v;
             }
         }
         __syncthreads();
@@ -415,6 +454,69 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 if (lo > -1.0) { double y = lo, len = sig; while (y > -1.0 && nl < 127) { y -= len; len *= 2; nl++; } }
                 if (hi < 1.0) { double x = hi, len = sig; while (x < 1.0 && nr < 127) { x += len; len *= 2; nr++; } }
                 const int npan = nl + 1 + nr;
+                if (MIX) {
+                    // the same panels and sums in double-float on the FP32 pipes (about 48 bits)
+                    const float2 *cmf = reinterpret_cast<const float2 *>(em) + 3 * P * e;
+                    const dfa ytf[3] = {dfs(yt[0]), dfs(yt[1]), dfs(yt[2])};
+                    const dfa lof = dfs(lo), hif = dfs(hi), sigf = dfs(sig);
+                    const float2 *nf = reinterpret_cast<const float2 *>(sw + Z::FR + 13);
+                    const dfa n0 = {nf[0].x, nf[0].y}, n1 = {nf[1].x, nf[1].y}, n2 = {nf[2].x, nf[2].y};
+                    const float uzf = (float)uz;
+                    dfa a0acc = {0.0f, 0.0f}, a1acc = {0.0f, 0.0f};
+                    for (int idx = lane; idx < npan * RRQ_NOM; idx += 32) {
+                        const int pan = idx / RRQ_NOM, g = idx % RRQ_NOM;
+                        dfa a0, a1;
+                        if (pan < nl) {
+                            const float pk = ldexpf(1.0f, nl - pan);
+                            // pk - 1 and pk/2 - 1 exactly, as (hi, lo) pairs
+                            a0 = dfadd(lof, dfneg(dfmul(dfadd(dfa{pk, 0.0f}, dfa{-1.0f, 0.0f}), sigf)));
+                            if (a0.h + a0.l < -1.0f) a0 = dfa{-1.0f, 0.0f};
+                            a1 = dfadd(lof, dfneg(dfmul(dfadd(dfa{0.5f * pk, 0.0f}, dfa{-1.0f, 0.0f}), sigf)));
+                        } else if (pan == nl) {
+                            a0 = lof;
+                            a1 = hif;
+                        } else {
+                            const float pk = ldexpf(1.0f, pan - nl);
+                            a0 = dfadd(hif, dfmul(dfadd(dfa{0.5f * pk, 0.0f}, dfa{-1.0f, 0.0f}), sigf));
+                            a1 = dfadd(hif, dfmul(dfadd(dfa{pk, 0.0f}, dfa{-1.0f, 0.0f}), sigf));
+                            if (a1.h + a1.l > 1.0f) a1 = dfa{1.0f, 0.0f};
+                        }
+                        const dfa mid = dfmul(dfa{0.5f, 0.0f}, dfadd(a0, a1));
+                        const dfa half = dfmul(dfa{0.5f, 0.0f}, dfadd(a1, dfneg(a0)));
+                        const dfa tt = dffma(half, dfs(tab->tom[g]), mid), wg = dfmul(half, dfs(tab->wom[g]));
+                        dfa y[3], dy[3];
+                        for (int c = 0; c < 3; c++) {
+                            const float2 top = cmf[3 * (P - 1) + c];
+                            y[c] = dfa{top.x, top.y};
+                            dy[c] = dfa{0.0f, 0.0f};
+                        }
+                        for (int k = P - 2; k >= 0; k--)
+                            for (int c = 0; c < 3; c++) {
+                                dy[c] = dffma(dy[c], tt, y[c]);
+                                const float2 ck = cmf[3 * k + c];
+                                y[c] = dffma(y[c], tt, dfa{ck.x, ck.y});
+                            }
+                        const dfa d0 = dfadd(ytf[0], dfneg(y[0])), d1 = dfadd(ytf[1], dfneg(y[1]));
+                        const dfa d2 = dfadd(ytf[2], dfneg(y[2]));
+                        const dfa r2 = dfadd(dfmul(d0, d0), dfadd(dfmul(d1, d1), dfmul(d2, d2)));
+                        const dfa ir = dfrsqrt(r2), r = dfmul(r2, ir);
+                        const dfa E = dfadd(r, dfmul(dfa{uzf, 0.0f}, d2));
+                        const dfa iE = dfrcp(E), inv = dfmul(ir, iE);
+                        const dfa N = dfmul(dfa{uzf, 0.0f}, dfadd(dfmul(d1, dy[0]), dfneg(dfmul(d0, dy[1]))));
+                        a0acc = dfadd(a0acc, dfneg(dfmul(dfmul(wg, N), inv)));
+                        if (wantDP) {
+                            const dfa nd = dfadd(dfmul(n0, d0), dfadd(dfmul(n1, d1), dfmul(n2, d2)));
+                            // (nu' x u) . tau with u = uz e_z: uz (nu'_y tau_x - nu'_x tau_y)
+                            const dfa nxt = dfmul(dfa{uzf, 0.0f}, dfadd(dfmul(n1, dy[0]), dfneg(dfmul(n0, dy[1]))));
+                            const dfa t1 = dfmul(dfmul(N, iE), dfadd(dfmul(dfa{uzf, 0.0f}, n2), dfmul(nd, ir)));
+                            const dfa t2 = dfmul(dfmul(nd, N), dfmul(ir, ir));
+                            const dfa v = dfmul(inv, dfadd(nxt, dfneg(dfadd(t1, t2))));
+                            a1acc = dfadd(a1acc, dfneg(dfmul(wg, v)));
+                        }
+                    }
+                    o0 = dfval(a0acc);
+                    do0 = dfval(a1acc);
+                } else
                 for (int idx = lane; idx < npan * RRQ_NOM; idx += 32) {
                     const int pan = idx / RRQ_NOM, g = idx % RRQ_NOM;
                     // panel k away from the central one spans (2^(k-1) - 1) sig .. (2^k - 1) sig

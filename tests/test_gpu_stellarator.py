@@ -93,7 +93,7 @@ def test_stellarator_sampled_rows(ctx, oracle_lib):
 
 def test_green_identity_high_order_density_given(ctx):
     """p = 10, 12: Green's identity through the matrix rows and through the density-given
-    evaluation; the latter keeps the digits the rows lose to rounding."""
+    evaluation agree (both apply the same fit matrices X to the density)."""
     rows, dens = {}, {}
     for p in (10, 12):
         d, tg = W.stellarator(p)
@@ -101,4 +101,5 @@ def test_green_identity_high_order_density_given(ctx):
         dens[p] = green_identity_error_density_given(ctx, d, tg)
     print("stellarator Green's identity at high order: matrix rows", {p: f"{e:.2e}" for p, e in rows.items()},
           "density-given", {p: f"{e:.2e}" for p, e in dens.items()})
-    assert dens[12] < rows[12] and dens[12] < dens[10]
+    for p in (10, 12):
+        assert abs(dens[p] - rows[p]) <= 0.05 * rows[p], (p, dens[p], rows[p])
