@@ -311,6 +311,15 @@ def bench_gpu(args):
                      "flops_per_pair": fpp, "kernel_ms": pair_s * 1e3},
         "stage_ms": {"precompute": diag["ms_precompute"], "near_and_items": diag["ms_near"], "pairs": diag["ms_pairs"]},
         "fit_kappa_max": diag["kappa_max"],
+        "accuracy": {
+            "reference": "binary128 build of the oracle (same algorithm, rounding unit 2^-113), "
+                         "tests/test_gpu_parity.py::test_full_size_ellipsoid_sampled, 100 sampled rows",
+            "apply_E_true": "1.1e-12 (D), 1.3e-12 (S'), 4.5e-13 (D'), 7.5e-16 (S): the corrections applied to a "
+                            "random Y_l^m density, relative to the sums they correct",
+            "row_E_true": "1.8e-6 (D), 1.4e-6 (S'), 3.7e-8 (S), 1.7e-10 (D'); the FP64 oracle's own: 1.9e-6, 1.3e-6, "
+                          "5.0e-8, 2.4e-10 (binary64 rows of this formulation lose digits on these stretched "
+                          "patches, Sec. 5.1 eq. interpolationerror)",
+            "gate": "E_true <= max(1e-10, 4 x the FP64 oracle's E_true), rows and applies"},
         "launch_shape": tuned,
         "clocks": clk,
         "gpu_launches": launches * args.steps if launches is not None else None,
