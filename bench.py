@@ -156,8 +156,9 @@ def flops_per_pair(p: int) -> float:
     njk = (p + 1) * (p + 2) // 2
     ns = 3 * pt
     n1, n2 = njk - 1, njk - 3                          # harmonics (j, k >= 0) with j >= 1, j >= 2
-    # Step 6: V (3 FMA x complex) for j >= 1; Q (18 FMA) and dQ/dnu' (24 FMA) for j >= 2
-    line = ns * (12 * n1 + 36 * n2 + 48 * n2)
+    # Step 6: V (3 FMA x complex) for j >= 1; for j >= 2 the product (0, d)(0, h) (18 FMA),
+    # Q and the w3 (nu'.d) sum of dQ/dnu' from it (8 FMA each), sum w1 h (6 FMA)
+    line = ns * (12 * n1 + 80 * n2)
     # Step 7: per (l, m >= 1), sum over (j, k): 5 flops for the psi term, 67 with Q, dQ, dS (j >= 2)
     trans = 0
     for l in range(1, p + 1):
@@ -289,6 +290,7 @@ def bench_gpu(args):
     if not args.no_batched and world == 1:
         legs["batched"] = batched_leg(ctx, dev)
         legs["stellarator"] = stellarator_leg(ctx, dev)
+        legs["translation"] = translation_leg(ctx, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
@@ -501,6 +503,36 @@ def stellarator_leg(ctx, dev) -> dict:
             ctx.csr_free(csr)
             res[k] = o.cpu().numpy()
         row["green_identity_rel_err"] = float(np.abs(res["S"] - res["D"] - 0.5 * u).max() / u.max())
+        out[f"p{p}"] = row
+    return out
+
+
+def translation_leg(ctx, dev) -> dict:
+    """Step 7 both ways: the direct O(p^4) translation sums (the default) against the O(p^3)
+    rotation-based translation (rrq_options.translation = 1, Sec. 2.3), FP64, all four
+    kernels, on the 320-patch star with every node a target, p = 6 ... 14: device time of
+    the per-pair stage (rrq_diag.ms_pairs) of one build each, after a warm-up build of each
+    form on the first 64 targets."""
+    from paper_2411_08342_gb300 import rrq
+    from paper_2411_08342_gb300 import workloads as W
+    out = {"workload": "star 320 patches, on-surface nodes, S D S' D' (FP64)"}
+    for p in (6, 8, 10, 12, 14):
+        d = W.discretize(W.star_surface(2), p)
+        tg = W.on_surface_targets(d)
+        few = W.Targets(tg.xyz[:64], tg.nrm[:64], tg.self_node[:64])
+        row = {"targets": tg.n}
+        for name, t in (("warm", few), ("time", tg)):
+            a = rrq.device_inputs(d, t, device=str(dev))
+            surf = ctx.surface(a["order"], a["node_off"], a["xyz"], a["nrm"], a["wts"], d.ref_uv)
+            targ = ctx.targets(a["txyz"], a["tnrm"], a["tself"])
+            for rot in (False, True):
+                csr = ctx.build_corrections(surf, targ, KERNELS, rotation=rot)
+                diag = ctx.diagnostics()
+                ctx.csr_free(csr)
+                if name == "time":
+                    row["pairs"] = int(diag["npairs"])
+                    row["ms_rotation" if rot else "ms_direct"] = float(diag["ms_pairs"])
+        row["rotation_over_direct"] = row["ms_rotation"] / row["ms_direct"]
         out[f"p{p}"] = row
     return out
 

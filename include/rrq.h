@@ -104,6 +104,17 @@ typedef struct {
                                 weights, Omega_0, target harmonics and the smooth subtraction
                                 stay FP64.  In rrq_apply: the smooth sum beyond r_c in FP32
                                 (see rrq_apply) */
+    int32_t translation;     /* Step 7.  0: the translation sums of eqs. l2ltranslation2-3 term
+                                by term, O(p^4) per pair (default).  1: the O(p^3) scheme of
+                                the remark on fast translation in Sec. 2.3 -- rotate the line
+                                integrals so that the target lies on the polar axis, translate
+                                along it, rotate back.  The same rows up to rounding.  Only
+                                for FP64 matrix builds (rrq_build_corrections,
+                                rrq_build_corrections_into; with precision = 1:
+                                RRQ_ERR_UNSUPPORTED; values other than 0, 1: RRQ_ERR_ARG);
+                                rrq_evaluate_near, rrq_batch_create and
+                                rrq_build_corrections_static return RRQ_ERR_UNSUPPORTED for
+                                any value but 0; rrq_apply ignores it */
 } rrq_options;
 
 /* CSR correction matrix in device memory owned by the library (rrq_csr_free). */

@@ -267,6 +267,7 @@ struct Prep {
     int64_t nnz = 0;
     BuildCounters *d_cnt = nullptr;
     bool mixed = false;
+    bool rot = false;      // rotation-based translation
     int newton_max = 30;
     double kappa_max = 0;  // max over patches of kappa_1(A)
 };
@@ -306,7 +307,13 @@ rrq_status build_prep(rrq_ctx *ctx, Scratch &s, const rrq_surface *surf, const r
     const double eta = o.eta > 0 ? o.eta : 1.0;
     pr.newton_max = o.newton_max > 0 ? o.newton_max : 30;
     if (o.precision != 0 && o.precision != 1) return RRQ_ERR_ARG;
+    if (o.translation != 0 && o.translation != 1) return RRQ_ERR_ARG;
+    if (o.translation == 1 && o.precision != 0) {
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rotation-based translation: FP64 builds only (precision = 0)");
+        return RRQ_ERR_UNSUPPORTED;
+    }
     pr.mixed = o.precision == 1;
+    pr.rot = o.translation == 1;
     const bool mixed = pr.mixed;
     Inputs &in = pr.in;
     rrq_status rs = prepare_inputs(ctx, s, surf, targ, o.inputs_on_host != 0, true, in);
@@ -453,9 +460,10 @@ extern "C" rrq_status rrq_build_corrections(rrq_ctx *ctx, const rrq_surface *sur
                 PatchData pdo = pd;
                 pdo.roots = roots + 3 * i0;
                 pdo.uside = uside + i0;
-                const PairArgs pa = {ctx->d_tab[p], items + i0, i1 - i0, pdo, in.node_off, in.xyz, in.nrm, in.wts,
-                                     in.txyz, in.tnrm, in.tself, kernel_mask, newton_max,
-                                     {vals[0], vals[1], vals[2], vals[3]}, col, d_cnt};
+                PairArgs pa = {ctx->d_tab[p], items + i0, i1 - i0, pdo, in.node_off, in.xyz, in.nrm, in.wts,
+                               in.txyz, in.tnrm, in.tself, kernel_mask, newton_max,
+                               {vals[0], vals[1], vals[2], vals[3]}, col, d_cnt};
+                pa.rot = pr.rot;
                 const PairShape shape{ctx->tune_tile[mixed][p], ctx->tune_pers[mixed][p], tile_ctr + p};
                 e = rrq_launch_pairs(p, mixed, pa, shape, s.st);
                 if (e != cudaSuccess) break;
@@ -560,7 +568,7 @@ extern "C" rrq_status rrq_evaluate_near(rrq_ctx *ctx, const rrq_surface *surf, c
     rrq_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.precision != 0) return RRQ_ERR_UNSUPPORTED;
+    if (o.precision != 0 || o.translation != 0) return RRQ_ERR_UNSUPPORTED;
     CK(cudaSetDevice(ctx->device));
     memset(&ctx->diag, 0, sizeof(ctx->diag));
     rrq_launch_counter() = 0;
@@ -708,10 +716,11 @@ extern "C" rrq_status rrq_build_corrections_into(rrq_ctx *ctx, const rrq_surface
             PatchData pdo = pr.pd;
             pdo.roots = roots + 3 * i0;
             pdo.uside = uside + i0;
-            const PairArgs pa = {ctx->d_tab[p], pr.items + i0, i1 - i0, pdo, pr.in.node_off, pr.in.xyz, pr.in.nrm,
-                                 pr.in.wts, pr.in.txyz, pr.in.tnrm, pr.in.tself, kernel_mask, pr.newton_max,
-                                 {(double *)d_val[0], (double *)d_val[1], (double *)d_val[2], (double *)d_val[3]},
-                                 (int32_t *)d_col, pr.d_cnt};
+            PairArgs pa = {ctx->d_tab[p], pr.items + i0, i1 - i0, pdo, pr.in.node_off, pr.in.xyz, pr.in.nrm,
+                           pr.in.wts, pr.in.txyz, pr.in.tnrm, pr.in.tself, kernel_mask, pr.newton_max,
+                           {(double *)d_val[0], (double *)d_val[1], (double *)d_val[2], (double *)d_val[3]},
+                           (int32_t *)d_col, pr.d_cnt};
+            pa.rot = pr.rot;
             const PairShape shape{ctx->tune_tile[pr.mixed][p], ctx->tune_pers[pr.mixed][p], tile_ctr + p};
             e = rrq_launch_pairs(p, pr.mixed, pa, shape, s.st);
         }
@@ -1262,6 +1271,10 @@ extern "C" rrq_status rrq_build_corrections_static(rrq_ctx *ctx, const rrq_surfa
     }
     if (o.precision != 0) {
         snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: FP64 only (precision = 0)");
+        return RRQ_ERR_UNSUPPORTED;
+    }
+    if (o.translation != 0) {
+        snprintf(rrq_err_buf(), RRQ_ERR_LEN, "rrq_build_corrections_static: direct translation only (translation = 0)");
         return RRQ_ERR_UNSUPPORTED;
     }
     const double eta = o.eta > 0 ? o.eta : 1.0;

@@ -401,6 +401,7 @@ extern "C" rrq_status rrq_batch_create(rrq_ctx *ctx, int32_t nsurf, const rrq_su
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     if (o.precision != 0 && o.precision != 1) return RRQ_ERR_ARG;
+    if (o.translation != 0) return RRQ_ERR_UNSUPPORTED;
     CK(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
     rrq_batch *b = new rrq_batch();

@@ -60,7 +60,18 @@ struct OrderTables {
                                                     // Lagrange function l_i (ab a-major, a + b < p)
     double Cjl[(RRQ_PMAX + 1) * (RRQ_PMAX + 1)];    // [l][j] C_{j,l} = (j-2)!(l-j)!/(l-1)!, j >= 2
     double Djl[(RRQ_PMAX + 1) * (RRQ_PMAX + 1)];    // [l][j] D_{j,l} = (j-1)!(l-j)!/l!, j >= 1
+    // Rotation of the degree-l harmonics by -90 and +90 degrees about the Y axis of their own
+    // frame, Rn_l^m(Ry(+-90) a) = sum_k Delta^{+-}_{mk} Rn_l^k(a), folded for coefficient sets
+    // with c_{-k} = (-1)^k conj(c_k): Re y_m = sum_{k>=0} A_{mk} Re c_k, Im y_m = sum_{k>=1}
+    // B_{mk} Im c_k.  Per degree l at rot_off(l): A- [(l+1)^2], B- [l^2], A+, B+ (row-major,
+    // B indexed from 1).  Used by the rotation-based translation (Sec. 2.3).
+    double Drot[2 * ((RRQ_PMAX + 1) * RRQ_PMAX * (2 * RRQ_PMAX + 1) / 3 + (RRQ_PMAX + 1) * RRQ_PMAX + RRQ_PMAX + 1)];
 };
+
+// offset of degree l in OrderTables::Drot
+__host__ __device__ __forceinline__ constexpr int rot_off(int l) {
+    return 2 * ((l - 1) * l * (2 * l - 1) / 3 + l * (l - 1) + l);
+}
 
 // Complex preimage of one (pair, edge): Re t0, Im t0, converged (0/1), singularity swap (0/1).
 struct EdgeRoot {
@@ -154,6 +165,7 @@ struct PairArgs {
     const double *coef;
     const double *sigma;
     double *res[4];
+    int rot;              // 1: rotation-based translation (FP64 matrix build, the default tile)
 };
 
 // Launch shape of the per-pair stage.

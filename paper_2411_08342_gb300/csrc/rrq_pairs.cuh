@@ -80,6 +80,14 @@ struct PairSm {
     static constexpr int PSI = BP + 4 * NP;                           // NP
     static constexpr int TOTAL = ev(mx(mx(EEND, QEND), PSI + NP));
     static_assert(9 * P <= 12 * NS && 4 * NJK <= 12 * NS, "region R too small");
+    // rotation-based translation only, appended: the second buffer of the nine coefficient
+    // sets (18 NJK), e^{ik theta} and e^{ik(phi + 90)} for k = 0..P, rho^n / n!, and nu' in
+    // the rotated frame
+    static constexpr int RY = TOTAL;
+    static constexpr int RPH = RY + 18 * NJK;
+    static constexpr int RRP = RPH + 4 * (P + 1);
+    static constexpr int RNU = RRP + P + 1;
+    static constexpr int TOTAL_ROT = ev(RNU + 3);
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -130,7 +130,7 @@ __device__ __forceinline__ void kitem(int f, int nt, int &pl, int &jk) {
     }
 }
 
-template <int P, bool MIX, int T, bool EVAL>
+template <int P, bool MIX, int T, bool EVAL, bool ROT>
 __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned long long *tile_ctr) {
     const OrderTables *__restrict__ tab = a.tab;
     const PairItem *__restrict__ items = a.items;
@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
     }
     if (tid < 5) bc[tid] = 0;
     const double inv4pi = 0.07957747154594767, sq2 = 1.4142135623730951;
-#define SW(pl) (smraw + (size_t)(pl) * Z::TOTAL)
+    constexpr int STRIDE = ROT ? Z::TOTAL_ROT : Z::TOTAL;   // doubles per pair
+#define SW(pl) (smraw + (size_t)(pl) * STRIDE)
     // tiles of T consecutive items: grid-stride, or (persistent launch) fetched from a counter
     for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
         __syncthreads();
@@ -413,6 +414,11 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             vv[3] = w1 * (t1 * d2 - t2 * d1); vv[4] = w1 * (t2 * d0 - t0 * d2); vv[5] = w1 * (t0 * d1 - t1 * d0);
             vv[6] = w1; vv[7] = 0.0; vv[8] = 0.0;
             vv[9] = w3n * d0; vv[10] = w3n * d1; vv[11] = w3n * d2;
+            if (!MIX && wantDP) {
+                // FP64 with D': w3 (nu'.d) and d itself, for the shared product (0, d)(0, h)
+                vv[7] = w3n;
+                vv[9] = d0; vv[10] = d1; vv[11] = d2;
+            }
             double *wv = sw + Z::WV;
             if (MIX) {
                 // the same 12 numbers as (hi, lo) float pairs, in the same slot
@@ -693,28 +699,32 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 if (hj) {
                     const cd *h = eh + ((size_t)q * NJK + jk) * 3;
                     const cd h0 = h[0], h1 = h[1], h2 = h[2];
-                    const double a0 = o[0], a1 = o[1], a2 = o[2];
-                    Q0r = fma(-a0, h0.x, fma(-a1, h1.x, fma(-a2, h2.x, Q0r)));
-                    Q0i = fma(-a0, h0.y, fma(-a1, h1.y, fma(-a2, h2.y, Q0i)));
-                    Q1r = fma(a1, h2.x, fma(-a2, h1.x, Q1r));
-                    Q1i = fma(a1, h2.y, fma(-a2, h1.y, Q1i));
-                    Q2r = fma(a2, h0.x, fma(-a0, h2.x, Q2r));
-                    Q2i = fma(a2, h0.y, fma(-a0, h2.y, Q2i));
-                    Q3r = fma(a0, h1.x, fma(-a1, h0.x, Q3r));
-                    Q3i = fma(a0, h1.y, fma(-a1, h0.y, Q3i));
                     if (wantDP) {
-                        const double w1 = o[6], m0 = o[9], m1 = o[10], m2 = o[11];
+                        // Q and E are sums of the same product (0, d)(0, h) = (-d.h, d x h),
+                        // weighted by w1 and by w3 (nu'.d): form it once
+                        const double w1 = o[6], sn = o[7], d0 = o[9], d1 = o[10], d2 = o[11];
+                        const double r0r = -fma(d0, h0.x, fma(d1, h1.x, d2 * h2.x));
+                        const double r0i = -fma(d0, h0.y, fma(d1, h1.y, d2 * h2.y));
+                        const double r1r = fma(d1, h2.x, -d2 * h1.x), r1i = fma(d1, h2.y, -d2 * h1.y);
+                        const double r2r = fma(d2, h0.x, -d0 * h2.x), r2i = fma(d2, h0.y, -d0 * h2.y);
+                        const double r3r = fma(d0, h1.x, -d1 * h0.x), r3i = fma(d0, h1.y, -d1 * h0.y);
+                        Q0r = fma(w1, r0r, Q0r); Q0i = fma(w1, r0i, Q0i); Q1r = fma(w1, r1r, Q1r); Q1i = fma(w1, r1i, Q1i);
+                        Q2r = fma(w1, r2r, Q2r); Q2i = fma(w1, r2i, Q2i); Q3r = fma(w1, r3r, Q3r); Q3i = fma(w1, r3i, Q3i);
+                        E0r = fma(sn, r0r, E0r); E0i = fma(sn, r0i, E0i); E1r = fma(sn, r1r, E1r); E1i = fma(sn, r1i, E1i);
+                        E2r = fma(sn, r2r, E2r); E2i = fma(sn, r2i, E2i); E3r = fma(sn, r3r, E3r); E3i = fma(sn, r3i, E3i);
                         D0r = fma(w1, h0.x, D0r); D0i = fma(w1, h0.y, D0i);
                         D1r = fma(w1, h1.x, D1r); D1i = fma(w1, h1.y, D1i);
                         D2r = fma(w1, h2.x, D2r); D2i = fma(w1, h2.y, D2i);
-                        E0r = fma(-m0, h0.x, fma(-m1, h1.x, fma(-m2, h2.x, E0r)));
-                        E0i = fma(-m0, h0.y, fma(-m1, h1.y, fma(-m2, h2.y, E0i)));
-                        E1r = fma(m1, h2.x, fma(-m2, h1.x, E1r));
-                        E1i = fma(m1, h2.y, fma(-m2, h1.y, E1i));
-                        E2r = fma(m2, h0.x, fma(-m0, h2.x, E2r));
-                        E2i = fma(m2, h0.y, fma(-m0, h2.y, E2i));
-                        E3r = fma(m0, h1.x, fma(-m1, h0.x, E3r));
-                        E3i = fma(m0, h1.y, fma(-m1, h0.y, E3i));
+                    } else {
+                        const double a0 = o[0], a1 = o[1], a2 = o[2];
+                        Q0r = fma(-a0, h0.x, fma(-a1, h1.x, fma(-a2, h2.x, Q0r)));
+                        Q0i = fma(-a0, h0.y, fma(-a1, h1.y, fma(-a2, h2.y, Q0i)));
+                        Q1r = fma(a1, h2.x, fma(-a2, h1.x, Q1r));
+                        Q1i = fma(a1, h2.y, fma(-a2, h1.y, Q1i));
+                        Q2r = fma(a2, h0.x, fma(-a0, h2.x, Q2r));
+                        Q2i = fma(a2, h0.y, fma(-a0, h2.y, Q2i));
+                        Q3r = fma(a0, h1.x, fma(-a1, h0.x, Q3r));
+                        Q3i = fma(a0, h1.y, fma(-a1, h0.y, Q3i));
                     }
                 }
             }
@@ -735,7 +745,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
         // L0: nu' derivative of the target harmonics, dS^{(n,q)} = grad S^{(n,q)}(y') . nu', per
         // (pair, (n, q >= 0)), into the per-sample vectors' space (dead after phase K)
         // (mixed: the target harmonics as double-float pairs too, beside it)
-        if (wantDP || MIX) {
+        if ((wantDP || MIX) && !ROT) {
             for (int f = tid; f < nt * NJK; f += nth) {
                 const int pl = f / NJK, jk = f % NJK;
                 double *sw = SW(pl);
@@ -752,15 +762,72 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
             __syncthreads();
         }
+        // I[gamma] (eq. gammalmdef) and the row vectors B, (0, nu') B, Psi, dB/dnu' of one (pair, (l, m))
+        // from its nine translated sums (imaginary parts)
+        auto finish_lm = [&](double *sw, int l, int m, int lm, double Ib0, double Ib1, double Ib2, double Ib3,
+                             double Ip, double dI0, double dI1, double dI2, double dI3) {
+            const double *nut = sw + Z::NUT, *Om = sw + Z::OM;
+            const cd *St = reinterpret_cast<const cd *>(sw + Z::ST), *gSt = reinterpret_cast<const cd *>(sw + Z::GST);
+            const cd *HSt = reinterpret_cast<const cd *>(sw + Z::HST);
+            const cd *g = gSt + 3 * jk_index(l, m);
+            const double W0 = Om[0], W1 = Om[1], W2 = Om[2], W3 = Om[3];
+            const cd G0 = cscale(cadd(cadd(cscale(g[0], W1), cscale(g[1], W2)), cscale(g[2], W3)), -1.0);
+            const cd G1 = cadd(cscale(g[0], W0), csub(cscale(g[2], W2), cscale(g[1], W3)));
+            const cd G2 = cadd(cscale(g[1], W0), csub(cscale(g[0], W3), cscale(g[2], W1)));
+            const cd G3 = cadd(cscale(g[2], W0), csub(cscale(g[1], W1), cscale(g[0], W2)));
+            const double fct = sq2 * inv4pi;
+            double *Bs = sw + Z::B, *Bds = sw + Z::BD;
+            const double B0 = fct * (Ib0 + G0.y), B1 = fct * (Ib1 + G1.y), B2 = fct * (Ib2 + G2.y), B3 = fct * (Ib3 + G3.y);
+            // (0, nu') B, whose product with the S' fit gives the S' row (eq. sprime1formrep)
+            const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
+            const double Bp0 = n0 * B1 + n1 * B2 + n2 * B3, Bp1 = B0 * n0 + (n1 * B3 - n2 * B2);
+            const double Bp2 = B0 * n1 + (n2 * B1 - n0 * B3), Bp3 = B0 * n2 + (n0 * B2 - n1 * B1);
+            const double psi = fct * (Ip + St[jk_index(l, m)].y * Om[0]);
+            if (MIX) {
+                // rows in double-float: the row phase reads (hi, lo) pairs in the same slots
+                float2 *Bf = reinterpret_cast<float2 *>(Bs) + 4 * lm, *Bpf = reinterpret_cast<float2 *>(sw + Z::BP) + 4 * lm;
+                Bf[0] = split2d(B0); Bf[1] = split2d(B1); Bf[2] = split2d(B2); Bf[3] = split2d(B3);
+                Bpf[0] = split2d(Bp0); Bpf[1] = split2d(Bp1); Bpf[2] = split2d(Bp2); Bpf[3] = split2d(Bp3);
+                reinterpret_cast<float2 *>(sw + Z::PSI)[lm] = split2d(psi);
+            } else {
+                Bs[4 * lm] = B0; Bs[4 * lm + 1] = B1; Bs[4 * lm + 2] = B2; Bs[4 * lm + 3] = B3;
+                double *Bp = sw + Z::BP + 4 * lm;
+                Bp[0] = Bp0; Bp[1] = Bp1; Bp[2] = Bp2; Bp[3] = Bp3;
+                sw[Z::PSI + lm] = psi;
+            }
+            if (wantDP) {
+                const double X0 = Om[4], X1 = Om[5], X2 = Om[6], X3 = Om[7];
+                const cd E0 = cscale(cadd(cadd(cscale(g[0], X1), cscale(g[1], X2)), cscale(g[2], X3)), -1.0);
+                const cd E1 = cadd(cscale(g[0], X0), csub(cscale(g[2], X2), cscale(g[1], X3)));
+                const cd E2 = cadd(cscale(g[1], X0), csub(cscale(g[0], X3), cscale(g[2], X1)));
+                const cd E3 = cadd(cscale(g[2], X0), csub(cscale(g[1], X1), cscale(g[0], X2)));
+                const cd *H = HSt + 6 * jk_index(l, m);
+                cd hn[3];
+                hn[0] = cadd(cadd(cscale(H[0], nut[0]), cscale(H[1], nut[1])), cscale(H[2], nut[2]));
+                hn[1] = cadd(cadd(cscale(H[1], nut[0]), cscale(H[3], nut[1])), cscale(H[4], nut[2]));
+                hn[2] = cadd(cadd(cscale(H[2], nut[0]), cscale(H[4], nut[1])), cscale(H[5], nut[2]));
+                const cd F0 = cscale(cadd(cadd(cscale(hn[0], W1), cscale(hn[1], W2)), cscale(hn[2], W3)), -1.0);
+                const cd F1 = cadd(cscale(hn[0], W0), csub(cscale(hn[2], W2), cscale(hn[1], W3)));
+                const cd F2 = cadd(cscale(hn[1], W0), csub(cscale(hn[0], W3), cscale(hn[2], W1)));
+                const cd F3 = cadd(cscale(hn[2], W0), csub(cscale(hn[1], W1), cscale(hn[0], W2)));
+                const double d0 = fct * (dI0 + E0.y + F0.y), d1 = fct * (dI1 + E1.y + F1.y);
+                const double d2 = fct * (dI2 + E2.y + F2.y), d3 = fct * (dI3 + E3.y + F3.y);
+                if (MIX) {
+                    float2 *Bdf = reinterpret_cast<float2 *>(Bds) + 4 * lm;
+                    Bdf[0] = split2d(d0); Bdf[1] = split2d(d1); Bdf[2] = split2d(d2); Bdf[3] = split2d(d3);
+                } else {
+                    Bds[4 * lm] = d0; Bds[4 * lm + 1] = d1; Bds[4 * lm + 2] = d2; Bds[4 * lm + 3] = d3;
+                }
+            }
+        };
         // L: translations and I[gamma], one thread per (pair, (l, m)); items ordered with
         // the largest l first and the pair index fastest, so that the lanes of a warp
         // run loops of similar length.  The factors C_{j,l}, D_{j,l} multiply each j's sum.
+        if constexpr (!ROT)
         for (int f = tid; f < nt * NP; f += nth) {
             const int pl = f % nt, lm = NP - 1 - f / nt;
             double *sw = SW(pl);
-            const double *nut = sw + Z::NUT, *Om = sw + Z::OM;
-            const cd *St = reinterpret_cast<const cd *>(sw + Z::ST), *gSt = reinterpret_cast<const cd *>(sw + Z::GST);
-            const cd *HSt = reinterpret_cast<const cd *>(sw + Z::HST), *Qs = reinterpret_cast<const cd *>(sw + Z::Q);
+            const cd *St = reinterpret_cast<const cd *>(sw + Z::ST), *Qs = reinterpret_cast<const cd *>(sw + Z::Q);
             const cd *dQs = reinterpret_cast<const cd *>(sw + Z::DQQ), *Vs = reinterpret_cast<const cd *>(sw + Z::V);
             const cd *dSt = reinterpret_cast<const cd *>(sw + Z::DST);
             int l = 1;
@@ -845,55 +912,202 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     }
                 }
             }
-            const cd *g = gSt + 3 * jk_index(l, m);
-            const double W0 = Om[0], W1 = Om[1], W2 = Om[2], W3 = Om[3];
-            const cd G0 = cscale(cadd(cadd(cscale(g[0], W1), cscale(g[1], W2)), cscale(g[2], W3)), -1.0);
-            const cd G1 = cadd(cscale(g[0], W0), csub(cscale(g[2], W2), cscale(g[1], W3)));
-            const cd G2 = cadd(cscale(g[1], W0), csub(cscale(g[0], W3), cscale(g[2], W1)));
-            const cd G3 = cadd(cscale(g[2], W0), csub(cscale(g[1], W1), cscale(g[0], W2)));
-            const double fct = sq2 * inv4pi;
-            double *Bs = sw + Z::B, *Bds = sw + Z::BD;
-            const double B0 = fct * (Ib0 + G0.y), B1 = fct * (Ib1 + G1.y), B2 = fct * (Ib2 + G2.y), B3 = fct * (Ib3 + G3.y);
-            // (0, nu') B, whose product with the S' fit gives the S' row (eq. sprime1formrep)
-            const double n0 = nut[0], n1 = nut[1], n2 = nut[2];
-            const double Bp0 = n0 * B1 + n1 * B2 + n2 * B3, Bp1 = B0 * n0 + (n1 * B3 - n2 * B2);
-            const double Bp2 = B0 * n1 + (n2 * B1 - n0 * B3), Bp3 = B0 * n2 + (n0 * B2 - n1 * B1);
-            const double psi = fct * (Ip + St[jk_index(l, m)].y * Om[0]);
-            if (MIX) {
-                // rows in double-float: the row phase reads (hi, lo) pairs in the same slots
-                float2 *Bf = reinterpret_cast<float2 *>(Bs) + 4 * lm, *Bpf = reinterpret_cast<float2 *>(sw + Z::BP) + 4 * lm;
-                Bf[0] = split2d(B0); Bf[1] = split2d(B1); Bf[2] = split2d(B2); Bf[3] = split2d(B3);
-                Bpf[0] = split2d(Bp0); Bpf[1] = split2d(Bp1); Bpf[2] = split2d(Bp2); Bpf[3] = split2d(Bp3);
-                reinterpret_cast<float2 *>(sw + Z::PSI)[lm] = split2d(psi);
-            } else {
-                Bs[4 * lm] = B0; Bs[4 * lm + 1] = B1; Bs[4 * lm + 2] = B2; Bs[4 * lm + 3] = B3;
-                double *Bp = sw + Z::BP + 4 * lm;
-                Bp[0] = Bp0; Bp[1] = Bp1; Bp[2] = Bp2; Bp[3] = Bp3;
-                sw[Z::PSI + lm] = psi;
-            }
-            if (wantDP) {
-                const double X0 = Om[4], X1 = Om[5], X2 = Om[6], X3 = Om[7];
-                const cd E0 = cscale(cadd(cadd(cscale(g[0], X1), cscale(g[1], X2)), cscale(g[2], X3)), -1.0);
-                const cd E1 = cadd(cscale(g[0], X0), csub(cscale(g[2], X2), cscale(g[1], X3)));
-                const cd E2 = cadd(cscale(g[1], X0), csub(cscale(g[0], X3), cscale(g[2], X1)));
-                const cd E3 = cadd(cscale(g[2], X0), csub(cscale(g[1], X1), cscale(g[0], X2)));
-                const cd *H = HSt + 6 * jk_index(l, m);
-                cd hn[3];
-                hn[0] = cadd(cadd(cscale(H[0], nut[0]), cscale(H[1], nut[1])), cscale(H[2], nut[2]));
-                hn[1] = cadd(cadd(cscale(H[1], nut[0]), cscale(H[3], nut[1])), cscale(H[4], nut[2]));
-                hn[2] = cadd(cadd(cscale(H[2], nut[0]), cscale(H[4], nut[1])), cscale(H[5], nut[2]));
-                const cd F0 = cscale(cadd(cadd(cscale(hn[0], W1), cscale(hn[1], W2)), cscale(hn[2], W3)), -1.0);
-                const cd F1 = cadd(cscale(hn[0], W0), csub(cscale(hn[2], W2), cscale(hn[1], W3)));
-                const cd F2 = cadd(cscale(hn[1], W0), csub(cscale(hn[0], W3), cscale(hn[2], W1)));
-                const cd F3 = cadd(cscale(hn[2], W0), csub(cscale(hn[1], W1), cscale(hn[0], W2)));
-                const double d0 = fct * (dI0 + E0.y + F0.y), d1 = fct * (dI1 + E1.y + F1.y);
-                const double d2 = fct * (dI2 + E2.y + F2.y), d3 = fct * (dI3 + E3.y + F3.y);
-                if (MIX) {
-                    float2 *Bdf = reinterpret_cast<float2 *>(Bds) + 4 * lm;
-                    Bdf[0] = split2d(d0); Bdf[1] = split2d(d1); Bdf[2] = split2d(d2); Bdf[3] = split2d(d3);
-                } else {
-                    Bds[4 * lm] = d0; Bds[4 * lm + 1] = d1; Bds[4 * lm + 2] = d2; Bds[4 * lm + 3] = d3;
+            finish_lm(sw, l, m, lm, Ib0, Ib1, Ib2, Ib3, Ip, dI0, dI1, dI2, dI3);
+        }
+        if constexpr (ROT) {
+            // Rotation-based translation (Sec. 2.3, the remark on fast translation), O(p^3) per
+            // pair: rotate the nine coefficient sets (set 0..3: the components of Q, 4..7: those
+            // of dQ/dnu', 8: V) so that y' lies on the polar axis of the harmonics, translate
+            // along that axis, where Rn_n^q(rho e_z) = rho^n / n! for q = 0 and 0 otherwise so
+            // that only the k = m terms remain, and rotate the results back.  With (theta, phi)
+            // the polar angles of y' in the harmonics' frame (X, Y, Z) = (y, z, x),
+            //   U = Ry(-theta) Rz(-phi) = Rz(90) Ry(90) Rz(-theta) Ry(-90) Rz(-phi - 90),
+            //   U^-1 = Rz(phi + 90) Ry(90) Rz(theta) Ry(-90) Rz(-90):
+            // z rotations are the phases e^{ik alpha}, the two fixed Y rotations the exact
+            // tables Delta+- (tab->Drot).  Every set keeps c_{-k} = (-1)^k conj(c_k), so only
+            // k >= 0 is held; the nu' derivative of the translation kernel, on the axis,
+            // couples k' = m', m' -+ 1 only (ladder rules of Rn).  Stages R0 .. R6.
+            auto cset = [&](double *sw, int s, int jk) -> double * {
+                return s < 4 ? sw + Z::Q + 2 * (4 * jk + s)
+                             : (s < 8 ? sw + Z::DQQ + 2 * (4 * jk + s - 4) : sw + Z::V + 2 * jk);
+            };
+            // folded product with a rotation table: (Delta v)_m for v at stride vs (doubles)
+            auto fold = [&](const double *D, int j, int m, const double *v, int vs) -> cd {
+                const double *A = D + m * (j + 1);
+                double re = 0.0, im = 0.0;
+                for (int k = 0; k <= j; k++) re = fma(A[k], v[k * vs], re);
+                if (m >= 1) {
+                    const double *B = D + (j + 1) * (j + 1) + (m - 1) * j;
+                    for (int k = 1; k <= j; k++) im = fma(B[k - 1], v[k * vs + 1], im);
                 }
+                return mkc(re, im);
+            };
+            auto dec = [](int jk, int &j, int &m) {
+                j = 0;
+                while ((j + 1) * (j + 2) / 2 <= jk) j++;
+                m = jk - j * (j + 1) / 2;
+            };
+            const double *Drot = tab->Drot;
+            const int nset = nt * 9 * NJK;
+            // R0: angles, the phases e^{ik theta}, e^{ik (phi + 90)}, rho^n / n!, U nu'
+            if (tid < nt) {
+                double *sw = SW(tid);
+                const double *yt = sw + Z::YT, *nut = sw + Z::NUT;
+                const double ax = yt[1], ay = yt[2], az = yt[0];
+                const double rxy = sqrt(ax * ax + ay * ay), rho = sqrt(rxy * rxy + az * az);
+                const double cph = rxy > 0.0 ? ax / rxy : 1.0, sph = rxy > 0.0 ? ay / rxy : 0.0;
+                const double cth = rho > 0.0 ? az / rho : 1.0, sth = rho > 0.0 ? rxy / rho : 0.0;
+                cd *eth = reinterpret_cast<cd *>(sw + Z::RPH), *eph = eth + (P + 1);
+                cd wt = mkc(1.0, 0.0), wp = mkc(1.0, 0.0);
+                const cd st = mkc(cth, sth), sp = mkc(-sph, cph);
+                for (int k = 0; k <= P; k++) {
+                    eth[k] = wt;
+                    eph[k] = wp;
+                    wt = cmul(wt, st);
+                    wp = cmul(wp, sp);
+                }
+                double *rp = sw + Z::RRP;
+                rp[0] = 1.0;
+                for (int n = 1; n <= P; n++) rp[n] = rp[n - 1] * rho * rcp_small(n);
+                const double nx = nut[1], ny = nut[2], nz = nut[0];
+                const double x1 = cph * nx + sph * ny, y1 = cph * ny - sph * nx;
+                sw[Z::RNU] = cth * x1 - sth * nz;
+                sw[Z::RNU + 1] = y1;
+                sw[Z::RNU + 2] = sth * x1 + cth * nz;
+            }
+            __syncthreads();
+            // R1: c <- Rz(-phi - 90) c, in place
+            for (int f = tid; f < nset; f += nth) {
+                const int pl = f % nt, r = f / nt, s = r % 9, jk = r / 9;
+                int j, k;
+                dec(jk, j, k);
+                if ((s >= 4 && s < 8 && !wantDP) || j < (s == 8 ? 1 : 2)) continue;
+                double *sw = SW(pl);
+                double *c = cset(sw, s, jk);
+                const cd e = reinterpret_cast<const cd *>(sw + Z::RPH)[P + 1 + k];
+                const double re = c[0], im = c[1];
+                c[0] = fma(re, e.x, im * e.y);
+                c[1] = fma(im, e.x, -re * e.y);
+            }
+            __syncthreads();
+            // R2: y = Rz(-theta) Ry(-90) c, into the second buffer (set-major)
+            for (int f = tid; f < nset; f += nth) {
+                const int pl = f % nt, r = f / nt, s = r % 9, jk = NJK - 1 - r / 9;
+                int j, m;
+                dec(jk, j, m);
+                if ((s >= 4 && s < 8 && !wantDP) || j < (s == 8 ? 1 : 2)) continue;
+                double *sw = SW(pl);
+                const cd y = fold(Drot + rot_off(j), j, m, cset(sw, s, jk - m), s == 8 ? 2 : 8);
+                const cd e = reinterpret_cast<const cd *>(sw + Z::RPH)[m];
+                reinterpret_cast<cd *>(sw + Z::RY)[s * NJK + jk] = cmul(y, cconj(e));
+            }
+            __syncthreads();
+            // R3: c' = Rz(90) Ry(90) y, back into the sets
+            for (int f = tid; f < nset; f += nth) {
+                const int pl = f % nt, r = f / nt, s = r % 9, jk = NJK - 1 - r / 9;
+                int j, m;
+                dec(jk, j, m);
+                if ((s >= 4 && s < 8 && !wantDP) || j < (s == 8 ? 1 : 2)) continue;
+                double *sw = SW(pl);
+                const int n1 = (j + 1) * (j + 1) + j * j;
+                const cd y = fold(Drot + rot_off(j) + n1, j, m, sw + Z::RY + 2 * (s * NJK + jk - m), 2);
+                double *c = cset(sw, s, jk);
+                const int q = m & 3;   // times i^m
+                c[0] = q == 0 ? y.x : (q == 1 ? -y.y : (q == 2 ? -y.x : y.y));
+                c[1] = q == 0 ? y.y : (q == 1 ? y.x : (q == 2 ? -y.y : -y.x));
+            }
+            __syncthreads();
+            // R4: translation along the axis, O'_{l m'} = sum_j W_{j,l} rho^{l-j}/(l-j)! c'_{j m'}
+            // (W = C for Q and dQ, D for V), plus for dQ the nu' derivative term acting on Q;
+            // then times (-i)^{m'} (the Rz(-90) that starts the inverse rotation)
+            for (int f = tid; f < nset; f += nth) {
+                const int pl = f % nt, r = f / nt, t = r % 9, jk = NJK - 1 - r / 9;
+                int l, mq;
+                dec(jk, l, mq);
+                if ((t >= 4 && t < 8 && !wantDP) || l < 1) continue;
+                double *sw = SW(pl);
+                const double *rp = sw + Z::RRP;
+                const double *Wl = (t == 8 ? tab->Djl : tab->Cjl) + l * (RRQ_PMAX + 1);
+                double ax = 0.0, ay = 0.0;
+                for (int j = max(t == 8 ? 1 : 2, mq); j <= l; j++) {
+                    const double w = Wl[j] * rp[l - j];
+                    const double *c = cset(sw, t, jk_index(j, mq));
+                    ax = fma(w, c[0], ax);
+                    ay = fma(w, c[1], ay);
+                }
+                if (t >= 4 && t < 8) {
+                    // grad Rn_n^q(rho e_z) . nu~ = rho^{n-1}/(n-1)! times nu~_z (q = 0),
+                    // (nu~_x + i nu~_y)/2 (q = 1), (-nu~_x + i nu~_y)/2 (q = -1); q = m' - k'
+                    const double nx = sw[Z::RNU], ny = sw[Z::RNU + 1], nz = sw[Z::RNU + 2];
+                    for (int j = 2; j < l; j++) {
+                        const double w = Wl[j] * rp[l - j - 1];
+                        if (mq <= j) {
+                            const double *c = cset(sw, t - 4, jk_index(j, mq));
+                            ax = fma(w * nz, c[0], ax);
+                            ay = fma(w * nz, c[1], ay);
+                        }
+                        if (mq - 1 <= j) {
+                            cd cv;
+                            if (mq >= 1) {
+                                const double *c = cset(sw, t - 4, jk_index(j, mq - 1));
+                                cv = mkc(c[0], c[1]);
+                            } else {   // c'_{j,-1} = -conj(c'_{j,1})
+                                const double *c = cset(sw, t - 4, jk_index(j, 1));
+                                cv = mkc(-c[0], c[1]);
+                            }
+                            const double gx = 0.5 * w * nx, gy = 0.5 * w * ny;
+                            ax = fma(gx, cv.x, fma(-gy, cv.y, ax));
+                            ay = fma(gx, cv.y, fma(gy, cv.x, ay));
+                        }
+                        if (mq + 1 <= j) {
+                            const double *c = cset(sw, t - 4, jk_index(j, mq + 1));
+                            const double gx = -0.5 * w * nx, gy = 0.5 * w * ny;
+                            ax = fma(gx, c[0], fma(-gy, c[1], ax));
+                            ay = fma(gx, c[1], fma(gy, c[0], ay));
+                        }
+                    }
+                }
+                const int q = mq & 3;   // times (-i)^{m'}
+                cd o;
+                o.x = q == 0 ? ax : (q == 1 ? ay : (q == 2 ? -ax : -ay));
+                o.y = q == 0 ? ay : (q == 1 ? -ax : (q == 2 ? -ay : ax));
+                reinterpret_cast<cd *>(sw + Z::RY)[t * NJK + jk] = o;
+            }
+            __syncthreads();
+            // R5: Rz(theta) Ry(-90), from the second buffer into the sets
+            for (int f = tid; f < nset; f += nth) {
+                const int pl = f % nt, r = f / nt, t = r % 9, jk = NJK - 1 - r / 9;
+                int l, m;
+                dec(jk, l, m);
+                if ((t >= 4 && t < 8 && !wantDP) || l < 1) continue;
+                double *sw = SW(pl);
+                const cd y = fold(Drot + rot_off(l), l, m, sw + Z::RY + 2 * (t * NJK + jk - m), 2);
+                const cd e = reinterpret_cast<const cd *>(sw + Z::RPH)[m];
+                const cd o = cmul(y, e);
+                double *c = cset(sw, t, jk);
+                c[0] = o.x;
+                c[1] = o.y;
+            }
+            __syncthreads();
+            // R6: per (pair, (l, m)), m >= 1: the nine sums, Im of Rz(phi + 90) Ry(90) applied to
+            // each set, then I[gamma] and the row vectors
+            for (int f = tid; f < nt * NP; f += nth) {
+                const int pl = f % nt, lm = NP - 1 - f / nt;
+                double *sw = SW(pl);
+                int l = 1;
+                while ((l + 1) * l / 2 <= lm) l++;
+                const int m = lm - l * (l - 1) / 2 + 1;
+                const double *D = Drot + rot_off(l) + (l + 1) * (l + 1) + l * l;
+                const cd e = reinterpret_cast<const cd *>(sw + Z::RPH)[P + 1 + m];
+                double o[9];
+#pragma unroll
+                for (int t = 0; t < 9; t++) {
+                    o[t] = 0.0;
+                    if (t >= 4 && t < 8 && !wantDP) continue;
+                    const cd u = fold(D, l, m, cset(sw, t, jk_index(l, 0)), t == 8 ? 2 : 8);
+                    o[t] = fma(e.y, u.x, e.x * u.y);
+                }
+                finish_lm(sw, l, m, lm, o[0], o[1], o[2], o[3], o[8], o[4], o[5], o[6], o[7]);
             }
         }
         __syncthreads();
@@ -1252,18 +1466,18 @@ __global__ void __launch_bounds__(128) k_uside(const PairItem *__restrict__ item
     pd.uside[n] = side;
 }
 
-template <int P, bool MIX, int T, bool EVAL = false>
+template <int P, bool MIX, int T, bool EVAL = false, bool ROT = false>
 cudaError_t launch_pairs_tile(const PairArgs &a, const PairShape &shape, cudaStream_t st) {
     constexpr int NTH = TileCfg<P>::THREADS;
-    const size_t bytes = sizeof(double) * PairSm<P>::TOTAL * T;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_pairs_tile<P, MIX, T, EVAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const size_t bytes = sizeof(double) * (ROT ? PairSm<P>::TOTAL_ROT : PairSm<P>::TOTAL) * T;
+    cudaError_t e = cudaFuncSetAttribute(k_pairs_tile<P, MIX, T, EVAL, ROT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     if (a.nitems <= 0) return cudaSuccess;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX, T, EVAL>, NTH, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_tile<P, MIX, T, EVAL, ROT>, NTH, bytes);
     if (per_sm < 1) per_sm = 1;
     k_roots<P><<<(unsigned)((a.nitems * 3 + 127) / 128), 128, 0, st>>>(a.tab, a.items, a.nitems, a.pd, a.txyz,
                                                                        a.newton_max);
@@ -1284,15 +1498,34 @@ cudaError_t launch_pairs_tile(const PairArgs &a, const PairShape &shape, cudaStr
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
     }
-    k_pairs_tile<P, MIX, T, EVAL><<<(unsigned)grid, NTH, bytes, st>>>(a, ctr);
+    k_pairs_tile<P, MIX, T, EVAL, ROT><<<(unsigned)grid, NTH, bytes, st>>>(a, ctr);
     RRQ_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
-// Dispatch on the tile size among the compiled ones (Ts, the first being the default).
+// Tile of the rotation-based translation: of the compiled tiles, the one that keeps the most
+// pairs resident per SM with its larger per-pair scratch (228 KB of shared memory per SM,
+// 1 KB reserved per CTA).
+template <int P, int... Ts>
+constexpr int rot_tile() {
+    int best = 0, bt = 0;
+    for (int t : {Ts...}) {
+        const int per_sm = (228 * 1024) / (t * PairSm<P>::TOTAL_ROT * 8 + 1024);
+        if (t * per_sm > best) {
+            best = t * per_sm;
+            bt = t;
+        }
+    }
+    return bt;
+}
+
+// Dispatch on the tile size among the compiled ones (Ts, the first being the default).  The
+// rotation-based translation (a.rot) is compiled for FP64 and one tile (rot_tile).
 template <int P, int... Ts>
 cudaError_t launch_pairs_order(bool mixed, const PairArgs &a, const PairShape &shape, cudaStream_t st) {
     constexpr int tiles[] = {Ts...};
+    if (a.rot)
+        return mixed ? cudaErrorInvalidValue : launch_pairs_tile<P, false, rot_tile<P, Ts...>(), false, true>(a, shape, st);
     const int T = shape.tile ? shape.tile : tiles[0];
     cudaError_t e = cudaErrorInvalidValue;
     ((T == Ts ? (void)(e = mixed ? launch_pairs_tile<P, true, Ts>(a, shape, st)

@@ -19,6 +19,46 @@
 
 namespace {
 
+// Rotation of Rn_l^m (Rn_l^m = R_l^m / sqrt((l-m)!(l+m)!)) by +90 degrees about the Y axis:
+// Rn_l^m(Ry(90) a) = sum_k Delta_{mk} Rn_l^k(a) with
+//     Delta_{mk} = 2^{-l} sum_s (-1)^{k-m+s} binom(l+k, k-m+s) binom(l-k, s),
+// Wigner's small-d formula at beta = pi/2 carried over to this normalisation (the
+// half-angle powers all become 2^{-1/2}).  The sum is of integers below 2^53, so every
+// entry is exact in double.  The -90 degree rotation is (-1)^{k-m} Delta_{mk}.  Both are
+// stored folded for coefficient sets with c_{-k} = (-1)^k conj(c_k) (see OrderTables).
+void rotation_tables(double *D) {
+    long long bn[2 * RRQ_PMAX + 1][2 * RRQ_PMAX + 1];
+    for (int n = 0; n <= 2 * RRQ_PMAX; n++)
+        for (int k = 0; k <= 2 * RRQ_PMAX; k++)
+            bn[n][k] = k == 0 ? 1 : (k > n ? 0 : bn[n - 1][k - 1] + (k <= n - 1 ? bn[n - 1][k] : 0));
+    for (int l = 0; l <= RRQ_PMAX; l++) {
+        auto delta = [&](int m, int k) {
+            long long acc = 0;
+            for (int s = 0; s <= l - k; s++) {
+                const int a = k - m + s;
+                if (a < 0 || a > l + k) continue;
+                const long long t = bn[l + k][a] * bn[l - k][s];
+                acc += ((k - m + s) & 1) ? -t : t;
+            }
+            return ldexp((double)acc, -l);
+        };
+        const int n1 = (l + 1) * (l + 1), n2 = l * l;
+        double *Am = D + rot_off(l), *Bm = Am + n1, *Ap = Bm + n2, *Bp = Ap + n1;
+        for (int sgn = 0; sgn < 2; sgn++) {
+            double *A = sgn ? Ap : Am, *B = sgn ? Bp : Bm;
+            auto d = [&](int m, int k) { return (sgn || !((k - m) & 1)) ? delta(m, k) : -delta(m, k); };
+            for (int m = 0; m <= l; m++) {
+                A[m * (l + 1)] = d(m, 0);
+                for (int k = 1; k <= l; k++) {
+                    const double pk = d(m, k), nk = (k & 1) ? -d(m, -k) : d(m, -k);
+                    A[m * (l + 1) + k] = pk + nk;
+                    if (m >= 1) B[(m - 1) * l + (k - 1)] = pk - nk;
+                }
+            }
+        }
+    }
+}
+
 // Gauss-Legendre on [-1,1]: Newton on P_n from Tricomi's initial approximation.
 void gl_rule(int n, double *x, double *w) {
     for (int k = 1; k <= n; k++) {
@@ -210,6 +250,7 @@ int rrq_host_order_tables(int p, int pt, double rho0, const double *ref_uv, Orde
                 T->Cjl[l * (RRQ_PMAX + 1) + j] = (in && j >= 2) ? f[j - 2] * f[l - j] / f[l - 1] : 0.0;
             }
     }
+    rotation_tables(T->Drot);
     // monomial coefficients of P_n by (n+1) P_{n+1} = (2n+1) t P_n - n P_{n-1}
     for (int i = 0; i < p * p; i++) T->L2M[i] = 0.0;
     T->L2M[0] = 1.0;

@@ -34,7 +34,8 @@ class TargetsS(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("inputs_on_host", C.c_int32), ("ptilde", C.c_int32), ("rho0", C.c_double),
-                ("newton_max", C.c_int32), ("eta", C.c_double), ("precision", C.c_int32)]
+                ("newton_max", C.c_int32), ("eta", C.c_double), ("precision", C.c_int32),
+                ("translation", C.c_int32)]
 
 
 class CSR(C.Structure):
@@ -225,11 +226,13 @@ class Context:
     # ------------------------------------------------------------- entry points
     def build_corrections(self, surf: Surface, targ: TargetsS, kernels=("S", "D", "SP", "DP"),
                           inputs_on_host: bool = False, rho0: float = 0.0, eta: float = 0.0,
-                          newton_max: int = 0, mixed: bool = False) -> CSR:
+                          newton_max: int = 0, mixed: bool = False, rotation: bool = False) -> CSR:
+        """rotation: the O(p^3) rotation-based translation of Step 7 instead of the direct
+        sums (rrq_options.translation = 1)."""
         mask = 0
         for k in kernels:
             mask |= KERNEL_BITS[k]
-        opt = Options(int(inputs_on_host), 0, rho0, newton_max, eta, int(mixed))
+        opt = Options(int(inputs_on_host), 0, rho0, newton_max, eta, int(mixed), int(rotation))
         out = CSR()
         st = self.L.rrq_build_corrections(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt), C.byref(out))
         _check(st, "rrq_build_corrections")
@@ -256,7 +259,7 @@ class Context:
 
     def build_corrections_into(self, surf: Surface, targ: TargetsS, rowptr, col, vals: dict,
                                kernels=("S", "D", "SP", "DP"), inputs_on_host: bool = False,
-                               mixed: bool = False, capacity: int = -1):
+                               mixed: bool = False, capacity: int = -1, rotation: bool = False):
         """Build into caller-owned buffers the device can address (torch CUDA tensors, or
         page-locked host memory as numpy views of pinned tensors): rowptr [ntarg+1] int64,
         col [capacity] int32, vals {kernel: [capacity] float64}.  The kernels write host
@@ -270,7 +273,7 @@ class Context:
             mask |= KERNEL_BITS[k]
             arr[KERNEL_SLOT[k]] = _ptr(vals[k]).value
         nnz, npairs = C.c_int64(), C.c_int64()
-        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, int(mixed))
+        opt = Options(int(inputs_on_host), 0, 0.0, 0, 0.0, int(mixed), int(rotation))
         st = self.L.rrq_build_corrections_into(self.h, C.byref(surf), C.byref(targ), mask, C.byref(opt),
                                                _ptr(rowptr), _ptr(col), arr, cap, C.byref(nnz), C.byref(npairs))
         self.last_nnz = nnz.value

@@ -176,19 +176,20 @@ def sub_csr(rowptr, col, vals, pos):
 
 
 def compare_with_oracle(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_host=False, sampled=False,
-                        label="", truth_max=300):
+                        label="", truth_max=300, **build_kw):
     """Build on the GPU; CSR structure exactly equal to the FP64 oracle's; values against
     the binary128 truth (rows and apply gates above), the difference to the FP64 oracle
     printed.  All rows, the rows tsel, or with sampled=True only the rows tsel copied back
     from a full-size build; the truth is formed on at most truth_max of those rows (a
-    seeded subset).  Returns ({kernel: E_true of the CUDA rows}, diag)."""
+    seeded subset).  build_kw goes to Context.build_corrections.  Returns ({kernel: E_true
+    of the CUDA rows}, diag)."""
     from paper_2411_08342_gb300 import workloads as W
     if sampled:
         # only the selected rows come back from the device; compare them directly
-        grp, gcol, gvals, diag = gpu_build_sampled(ctx, d, tg, tsel, kernels)
+        grp, gcol, gvals, diag = gpu_build_sampled(ctx, d, tg, tsel, kernels, **build_kw)
         tsel = np.asarray(tsel)
     else:
-        rowptr, col, vals, diag = gpu_build(ctx, d, tg, kernels, on_host=on_host)
+        rowptr, col, vals, diag = gpu_build(ctx, d, tg, kernels, on_host=on_host, **build_kw)
         if tsel is None:
             grp, gcol, gvals = rowptr, col, vals
         else:
