@@ -1166,82 +1166,50 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 }
             }
         } else
-        // M: rows through the fit matrices (Step 8), jump and smooth subtraction; one thread per
-        // (kernel group, pair, node), groups {D, D'} (X_D), {S'} (X_S'), {S} (X_S2, X_S1)
-        for (int f = tid; f < nt * NP * ngrp; f += nth) {
-            const int grp = s_grp[f / (nt * NP)], rem = f % (nt * NP), pl = rem / NP, i = rem % NP;
+        {
+        // M: rows through the fit matrices (Step 8), jump and smooth subtraction, for the kernel
+        // groups {D, D'} (X_D), {S'} (X_S'), {S} (X_S2, X_S1).  When every pair of the tile is on
+        // one patch (the usual case: the work list is grouped by patch), one thread per
+        // (group, node) reads each fit-matrix entry once and applies it to all the tile's pairs;
+        // otherwise one thread per (group, pair, node).  Both forms take the same operations in
+        // the same order for a pair, so its rows do not depend on the tile it falls in.
+        // fit-matrix terms of the lm-th harmonic at one node, FP64 (fused into the sums)
+        auto term_d = [&](double &r0, double &r1, const double *B, const double *Bd, double x0, double x1, double x2,
+                          double x3) {
+            r0 = fma(B[3], x3, fma(B[2], x2, fma(B[1], x1, fma(-B[0], x0, r0))));
+            if (wantDP) r1 = fma(Bd[3], x3, fma(Bd[2], x2, fma(Bd[1], x1, fma(-Bd[0], x0, r1))));
+        };
+        auto term_sp = [&](double &r0, const double *Bp, double x0, double x1, double x2, double x3) {
+            r0 = fma(Bp[3], x3, fma(Bp[2], x2, fma(Bp[1], x1, fma(Bp[0], x0, r0))));
+        };
+        auto term_s = [&](double &r0, const double *B, double psi, double xs1, double g0, double g1, double g2,
+                          double g3) {
+            r0 = fma(B[3], g3, fma(B[2], g2, fma(B[1], g1, fma(-B[0], g0, fma(psi, xs1, r0)))));
+        };
+        // the same in double-float with the (hi, lo) fit matrices
+        auto mterm_d = [&](dfa &a0, dfa &a1, const float2 *Bf, const float2 *Bdf, float2 x0, float2 x1, float2 x2,
+                           float2 x3) {
+            dfmac(a0, -Bf[0].x, -Bf[0].y, x0.x, x0.y); dfmac(a0, Bf[1].x, Bf[1].y, x1.x, x1.y);
+            dfmac(a0, Bf[2].x, Bf[2].y, x2.x, x2.y); dfmac(a0, Bf[3].x, Bf[3].y, x3.x, x3.y);
+            if (wantDP) {
+                dfmac(a1, -Bdf[0].x, -Bdf[0].y, x0.x, x0.y); dfmac(a1, Bdf[1].x, Bdf[1].y, x1.x, x1.y);
+                dfmac(a1, Bdf[2].x, Bdf[2].y, x2.x, x2.y); dfmac(a1, Bdf[3].x, Bdf[3].y, x3.x, x3.y);
+            }
+        };
+        auto mterm_sp = [&](dfa &a0, const float2 *Bpf, float2 x0, float2 x1, float2 x2, float2 x3) {
+            dfmac(a0, Bpf[0].x, Bpf[0].y, x0.x, x0.y); dfmac(a0, Bpf[1].x, Bpf[1].y, x1.x, x1.y);
+            dfmac(a0, Bpf[2].x, Bpf[2].y, x2.x, x2.y); dfmac(a0, Bpf[3].x, Bpf[3].y, x3.x, x3.y);
+        };
+        auto mterm_s = [&](dfa &a0, const float2 *Bf, float2 psi, float2 xs1, float2 g0, float2 g1, float2 g2,
+                           float2 g3) {
+            dfmac(a0, psi.x, psi.y, xs1.x, xs1.y);
+            dfmac(a0, -Bf[0].x, -Bf[0].y, g0.x, g0.y); dfmac(a0, Bf[1].x, Bf[1].y, g1.x, g1.y);
+            dfmac(a0, Bf[2].x, Bf[2].y, g2.x, g2.y); dfmac(a0, Bf[3].x, Bf[3].y, g3.x, g3.y);
+        };
+        // jump on self pairs, else minus the smooth rule; then the CSR entries of (pair, node)
+        auto finish_row = [&](int pl, int grp, int i, double r0, double r1) {
             const double *sw = SW(pl);
             const PairItem im = s_item[pl];
-            const size_t ps = (size_t)im.P;
-            const double *fr = sw + Z::FR;
-            const double sc = fr[12];
-            double r0 = 0, r1 = 0;  // group 0: D, D'; group 1: S'; group 2: S
-            if (MIX) {
-                // double-float dot products with the (hi, lo) fit matrices
-                dfa a0 = {0, 0}, a1 = {0, 0};
-                if (grp == 0) {
-                    const float2 *X = pd.XD2 + ps * pd_X(pd.pmax);
-                    const float2 *Bf = reinterpret_cast<const float2 *>(sw + Z::B), *Bdf = reinterpret_cast<const float2 *>(sw + Z::BD);
-                    for (int lm = 0; lm < NP; lm++) {
-                        const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
-                        const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
-                        const float2 b0 = Bf[4 * lm], b1 = Bf[4 * lm + 1], b2 = Bf[4 * lm + 2], b3 = Bf[4 * lm + 3];
-                        dfmac(a0, -b0.x, -b0.y, x0.x, x0.y); dfmac(a0, b1.x, b1.y, x1.x, x1.y);
-                        dfmac(a0, b2.x, b2.y, x2.x, x2.y); dfmac(a0, b3.x, b3.y, x3.x, x3.y);
-                        if (wantDP) {
-                            const float2 c0 = Bdf[4 * lm], c1 = Bdf[4 * lm + 1], c2 = Bdf[4 * lm + 2], c3 = Bdf[4 * lm + 3];
-                            dfmac(a1, -c0.x, -c0.y, x0.x, x0.y); dfmac(a1, c1.x, c1.y, x1.x, x1.y);
-                            dfmac(a1, c2.x, c2.y, x2.x, x2.y); dfmac(a1, c3.x, c3.y, x3.x, x3.y);
-                        }
-                    }
-                    r0 = dfval(a0);
-                    r1 = dfval(a1) * sc;
-                } else if (grp == 1) {
-                    const float2 *X = pd.XSp2 + ps * pd_X(pd.pmax), *Bpf = reinterpret_cast<const float2 *>(sw + Z::BP);
-                    for (int lm = 0; lm < NP; lm++)
-                        for (int c = 0; c < 4; c++) {
-                            const float2 x = X[(c * NP + lm) * NP + i], b = Bpf[4 * lm + c];
-                            dfmac(a0, b.x, b.y, x.x, x.y);
-                        }
-                    r0 = dfval(a0);
-                } else {
-                    const float2 *X = pd.XS22 + ps * pd_X(pd.pmax), *X1 = pd.XS12 + ps * pd_XS1(pd.pmax);
-                    const float2 *Bf = reinterpret_cast<const float2 *>(sw + Z::B), *Pf = reinterpret_cast<const float2 *>(sw + Z::PSI);
-                    for (int lm = 0; lm < NP; lm++) {
-                        const float2 x1 = X1[lm * NP + i], ps_ = Pf[lm];
-                        dfmac(a0, ps_.x, ps_.y, x1.x, x1.y);
-                        const float2 b0 = Bf[4 * lm], b1 = Bf[4 * lm + 1], b2 = Bf[4 * lm + 2], b3 = Bf[4 * lm + 3];
-                        const float2 g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
-                        const float2 g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
-                        dfmac(a0, -b0.x, -b0.y, g0.x, g0.y); dfmac(a0, b1.x, b1.y, g1.x, g1.y);
-                        dfmac(a0, b2.x, b2.y, g2.x, g2.y); dfmac(a0, b3.x, b3.y, g3.x, g3.y);
-                    }
-                    r0 = dfval(a0) * (1.0 / sc);
-                }
-            } else if (grp == 0) {
-                const double *X = pd.XD + ps * pd_X(pd.pmax), *Bs = sw + Z::B, *Bds = sw + Z::BD;
-                for (int lm = 0; lm < NP; lm++) {
-                    const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
-                    const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
-                    r0 -= Bs[4 * lm] * x0 - Bs[4 * lm + 1] * x1 - Bs[4 * lm + 2] * x2 - Bs[4 * lm + 3] * x3;
-                    if (wantDP)
-                        r1 -= Bds[4 * lm] * x0 - Bds[4 * lm + 1] * x1 - Bds[4 * lm + 2] * x2 - Bds[4 * lm + 3] * x3;
-                }
-                r1 *= sc;
-            } else if (grp == 1) {
-                const double *X = pd.XSp + ps * pd_X(pd.pmax), *Bp = sw + Z::BP;
-                for (int lm = 0; lm < NP; lm++)
-                    r0 += Bp[4 * lm] * X[(0 * NP + lm) * NP + i] + Bp[4 * lm + 1] * X[(1 * NP + lm) * NP + i] +
-                          Bp[4 * lm + 2] * X[(2 * NP + lm) * NP + i] + Bp[4 * lm + 3] * X[(3 * NP + lm) * NP + i];
-            } else {
-                const double *X = pd.XS2 + ps * pd_X(pd.pmax), *X1 = pd.XS1 + ps * pd_XS1(pd.pmax), *Bs = sw + Z::B;
-                const double *Psis = sw + Z::PSI;
-                for (int lm = 0; lm < NP; lm++)
-                    r0 += Psis[lm] * X1[lm * NP + i] -
-                          (Bs[4 * lm] * X[(0 * NP + lm) * NP + i] - Bs[4 * lm + 1] * X[(1 * NP + lm) * NP + i] -
-                           Bs[4 * lm + 2] * X[(2 * NP + lm) * NP + i] - Bs[4 * lm + 3] * X[(3 * NP + lm) * NP + i]);
-                r0 *= 1.0 / sc;
-            }
             const int64_t o = node_off[im.P];
             const int64_t dst = im.off + i;
             if (i == s_self[pl]) {
@@ -1273,6 +1241,144 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             } else if (vS) {
                 vS[dst] = r0;
             }
+        };
+        const size_t ps0 = (size_t)s_item[0].P;
+        if (s_item[nt - 1].P == s_item[0].P) {
+            const double sc = SW(0)[Z::FR + 12];
+            for (int f = tid; f < NP * ngrp; f += nth) {
+                const int grp = s_grp[f / NP], i = f % NP;
+                double r0[T], r1[T];
+                if (MIX) {
+                    dfa a0[T], a1[T];
+#pragma unroll
+                    for (int pl = 0; pl < T; pl++) a0[pl] = a1[pl] = dfa{0.f, 0.f};
+                    if (grp == 0) {
+                        const float2 *X = pd.XD2 + ps0 * pd_X(pd.pmax);
+                        for (int lm = 0; lm < NP; lm++) {
+                            const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
+                            const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
+#pragma unroll
+                            for (int pl = 0; pl < T; pl++)
+                                if (pl < nt)
+                                    mterm_d(a0[pl], a1[pl], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
+                                            reinterpret_cast<const float2 *>(SW(pl) + Z::BD) + 4 * lm, x0, x1, x2, x3);
+                        }
+                    } else if (grp == 1) {
+                        const float2 *X = pd.XSp2 + ps0 * pd_X(pd.pmax);
+                        for (int lm = 0; lm < NP; lm++) {
+                            const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
+                            const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
+#pragma unroll
+                            for (int pl = 0; pl < T; pl++)
+                                if (pl < nt)
+                                    mterm_sp(a0[pl], reinterpret_cast<const float2 *>(SW(pl) + Z::BP) + 4 * lm, x0, x1, x2,
+                                             x3);
+                        }
+                    } else {
+                        const float2 *X = pd.XS22 + ps0 * pd_X(pd.pmax), *X1 = pd.XS12 + ps0 * pd_XS1(pd.pmax);
+                        for (int lm = 0; lm < NP; lm++) {
+                            const float2 xs1 = X1[lm * NP + i];
+                            const float2 g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
+                            const float2 g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
+#pragma unroll
+                            for (int pl = 0; pl < T; pl++)
+                                if (pl < nt)
+                                    mterm_s(a0[pl], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
+                                            reinterpret_cast<const float2 *>(SW(pl) + Z::PSI)[lm], xs1, g0, g1, g2, g3);
+                        }
+                    }
+#pragma unroll
+                    for (int pl = 0; pl < T; pl++) {
+                        r0[pl] = dfval(a0[pl]);
+                        r1[pl] = dfval(a1[pl]);
+                    }
+                } else {
+#pragma unroll
+                    for (int pl = 0; pl < T; pl++) r0[pl] = r1[pl] = 0.0;
+                    if (grp == 0) {
+                        const double *X = pd.XD + ps0 * pd_X(pd.pmax);
+                        for (int lm = 0; lm < NP; lm++) {
+                            const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
+                            const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
+#pragma unroll
+                            for (int pl = 0; pl < T; pl++)
+                                if (pl < nt)
+                                    term_d(r0[pl], r1[pl], SW(pl) + Z::B + 4 * lm, SW(pl) + Z::BD + 4 * lm, x0, x1, x2, x3);
+                        }
+                    } else if (grp == 1) {
+                        const double *X = pd.XSp + ps0 * pd_X(pd.pmax);
+                        for (int lm = 0; lm < NP; lm++) {
+                            const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
+                            const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
+#pragma unroll
+                            for (int pl = 0; pl < T; pl++)
+                                if (pl < nt) term_sp(r0[pl], SW(pl) + Z::BP + 4 * lm, x0, x1, x2, x3);
+                        }
+                    } else {
+                        const double *X = pd.XS2 + ps0 * pd_X(pd.pmax), *X1 = pd.XS1 + ps0 * pd_XS1(pd.pmax);
+                        for (int lm = 0; lm < NP; lm++) {
+                            const double xs1 = X1[lm * NP + i];
+                            const double g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
+                            const double g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
+#pragma unroll
+                            for (int pl = 0; pl < T; pl++)
+                                if (pl < nt) term_s(r0[pl], SW(pl) + Z::B + 4 * lm, SW(pl)[Z::PSI + lm], xs1, g0, g1, g2, g3);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int pl = 0; pl < T; pl++)
+                    if (pl < nt)
+                        finish_row(pl, grp, i, grp == 2 ? r0[pl] * (1.0 / sc) : r0[pl], r1[pl] * sc);
+            }
+        } else
+        for (int f = tid; f < nt * NP * ngrp; f += nth) {
+            const int grp = s_grp[f / (nt * NP)], rem = f % (nt * NP), pl = rem / NP, i = rem % NP;
+            const double *sw = SW(pl);
+            const size_t ps = (size_t)s_item[pl].P;
+            const double sc = sw[Z::FR + 12];
+            double r0 = 0, r1 = 0;
+            if (MIX) {
+                dfa a0 = {0, 0}, a1 = {0, 0};
+                if (grp == 0) {
+                    const float2 *X = pd.XD2 + ps * pd_X(pd.pmax);
+                    for (int lm = 0; lm < NP; lm++)
+                        mterm_d(a0, a1, reinterpret_cast<const float2 *>(sw + Z::B) + 4 * lm,
+                                reinterpret_cast<const float2 *>(sw + Z::BD) + 4 * lm, X[(0 * NP + lm) * NP + i],
+                                X[(1 * NP + lm) * NP + i], X[(2 * NP + lm) * NP + i], X[(3 * NP + lm) * NP + i]);
+                } else if (grp == 1) {
+                    const float2 *X = pd.XSp2 + ps * pd_X(pd.pmax);
+                    for (int lm = 0; lm < NP; lm++)
+                        mterm_sp(a0, reinterpret_cast<const float2 *>(sw + Z::BP) + 4 * lm, X[(0 * NP + lm) * NP + i],
+                                 X[(1 * NP + lm) * NP + i], X[(2 * NP + lm) * NP + i], X[(3 * NP + lm) * NP + i]);
+                } else {
+                    const float2 *X = pd.XS22 + ps * pd_X(pd.pmax), *X1 = pd.XS12 + ps * pd_XS1(pd.pmax);
+                    for (int lm = 0; lm < NP; lm++)
+                        mterm_s(a0, reinterpret_cast<const float2 *>(sw + Z::B) + 4 * lm,
+                                reinterpret_cast<const float2 *>(sw + Z::PSI)[lm], X1[lm * NP + i],
+                                X[(0 * NP + lm) * NP + i], X[(1 * NP + lm) * NP + i], X[(2 * NP + lm) * NP + i],
+                                X[(3 * NP + lm) * NP + i]);
+                }
+                r0 = dfval(a0);
+                r1 = dfval(a1);
+            } else if (grp == 0) {
+                const double *X = pd.XD + ps * pd_X(pd.pmax);
+                for (int lm = 0; lm < NP; lm++)
+                    term_d(r0, r1, sw + Z::B + 4 * lm, sw + Z::BD + 4 * lm, X[(0 * NP + lm) * NP + i],
+                           X[(1 * NP + lm) * NP + i], X[(2 * NP + lm) * NP + i], X[(3 * NP + lm) * NP + i]);
+            } else if (grp == 1) {
+                const double *X = pd.XSp + ps * pd_X(pd.pmax);
+                for (int lm = 0; lm < NP; lm++)
+                    term_sp(r0, sw + Z::BP + 4 * lm, X[(0 * NP + lm) * NP + i], X[(1 * NP + lm) * NP + i],
+                            X[(2 * NP + lm) * NP + i], X[(3 * NP + lm) * NP + i]);
+            } else {
+                const double *X = pd.XS2 + ps * pd_X(pd.pmax), *X1 = pd.XS1 + ps * pd_XS1(pd.pmax);
+                for (int lm = 0; lm < NP; lm++)
+                    term_s(r0, sw + Z::B + 4 * lm, sw[Z::PSI + lm], X1[lm * NP + i], X[(0 * NP + lm) * NP + i],
+                           X[(1 * NP + lm) * NP + i], X[(2 * NP + lm) * NP + i], X[(3 * NP + lm) * NP + i]);
+            }
+            finish_row(pl, grp, i, grp == 2 ? r0 * (1.0 / sc) : r0, r1 * sc);
+        }
         }
     }
 #undef SW
