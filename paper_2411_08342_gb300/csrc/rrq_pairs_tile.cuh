@@ -1245,22 +1245,24 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
         const size_t ps0 = (size_t)s_item[0].P;
         if (s_item[nt - 1].P == s_item[0].P) {
             const double sc = SW(0)[Z::FR + 12];
-            for (int f = tid; f < NP * ngrp; f += nth) {
-                const int grp = s_grp[f / NP], i = f % NP;
+            // G groups of the tile's pairs (pairs g, g + G, ...) so that the items fill the CTA
+            const int nit = NP * ngrp, G = max(1, min(nt, nth / nit));
+            for (int f = tid; f < nit * G; f += nth) {
+                const int g = f / nit, grp = s_grp[(f % nit) / NP], i = f % NP;
                 double r0[T], r1[T];
                 if (MIX) {
                     dfa a0[T], a1[T];
 #pragma unroll
-                    for (int pl = 0; pl < T; pl++) a0[pl] = a1[pl] = dfa{0.f, 0.f};
+                    for (int u = 0, pl = g; u < T; u++, pl += G) a0[u] = a1[u] = dfa{0.f, 0.f};
                     if (grp == 0) {
                         const float2 *X = pd.XD2 + ps0 * pd_X(pd.pmax);
                         for (int lm = 0; lm < NP; lm++) {
                             const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
                             const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
 #pragma unroll
-                            for (int pl = 0; pl < T; pl++)
+                            for (int u = 0, pl = g; u < T; u++, pl += G)
                                 if (pl < nt)
-                                    mterm_d(a0[pl], a1[pl], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
+                                    mterm_d(a0[u], a1[u], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
                                             reinterpret_cast<const float2 *>(SW(pl) + Z::BD) + 4 * lm, x0, x1, x2, x3);
                         }
                     } else if (grp == 1) {
@@ -1269,9 +1271,9 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                             const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
                             const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
 #pragma unroll
-                            for (int pl = 0; pl < T; pl++)
+                            for (int u = 0, pl = g; u < T; u++, pl += G)
                                 if (pl < nt)
-                                    mterm_sp(a0[pl], reinterpret_cast<const float2 *>(SW(pl) + Z::BP) + 4 * lm, x0, x1, x2,
+                                    mterm_sp(a0[u], reinterpret_cast<const float2 *>(SW(pl) + Z::BP) + 4 * lm, x0, x1, x2,
                                              x3);
                         }
                     } else {
@@ -1281,29 +1283,29 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                             const float2 g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
                             const float2 g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
 #pragma unroll
-                            for (int pl = 0; pl < T; pl++)
+                            for (int u = 0, pl = g; u < T; u++, pl += G)
                                 if (pl < nt)
-                                    mterm_s(a0[pl], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
+                                    mterm_s(a0[u], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
                                             reinterpret_cast<const float2 *>(SW(pl) + Z::PSI)[lm], xs1, g0, g1, g2, g3);
                         }
                     }
 #pragma unroll
-                    for (int pl = 0; pl < T; pl++) {
-                        r0[pl] = dfval(a0[pl]);
-                        r1[pl] = dfval(a1[pl]);
+                    for (int u = 0, pl = g; u < T; u++, pl += G) {
+                        r0[u] = dfval(a0[u]);
+                        r1[u] = dfval(a1[u]);
                     }
                 } else {
 #pragma unroll
-                    for (int pl = 0; pl < T; pl++) r0[pl] = r1[pl] = 0.0;
+                    for (int u = 0, pl = g; u < T; u++, pl += G) r0[u] = r1[u] = 0.0;
                     if (grp == 0) {
                         const double *X = pd.XD + ps0 * pd_X(pd.pmax);
                         for (int lm = 0; lm < NP; lm++) {
                             const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
                             const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
 #pragma unroll
-                            for (int pl = 0; pl < T; pl++)
+                            for (int u = 0, pl = g; u < T; u++, pl += G)
                                 if (pl < nt)
-                                    term_d(r0[pl], r1[pl], SW(pl) + Z::B + 4 * lm, SW(pl) + Z::BD + 4 * lm, x0, x1, x2, x3);
+                                    term_d(r0[u], r1[u], SW(pl) + Z::B + 4 * lm, SW(pl) + Z::BD + 4 * lm, x0, x1, x2, x3);
                         }
                     } else if (grp == 1) {
                         const double *X = pd.XSp + ps0 * pd_X(pd.pmax);
@@ -1311,8 +1313,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                             const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
                             const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
 #pragma unroll
-                            for (int pl = 0; pl < T; pl++)
-                                if (pl < nt) term_sp(r0[pl], SW(pl) + Z::BP + 4 * lm, x0, x1, x2, x3);
+                            for (int u = 0, pl = g; u < T; u++, pl += G)
+                                if (pl < nt) term_sp(r0[u], SW(pl) + Z::BP + 4 * lm, x0, x1, x2, x3);
                         }
                     } else {
                         const double *X = pd.XS2 + ps0 * pd_X(pd.pmax), *X1 = pd.XS1 + ps0 * pd_XS1(pd.pmax);
@@ -1321,15 +1323,15 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                             const double g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
                             const double g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
 #pragma unroll
-                            for (int pl = 0; pl < T; pl++)
-                                if (pl < nt) term_s(r0[pl], SW(pl) + Z::B + 4 * lm, SW(pl)[Z::PSI + lm], xs1, g0, g1, g2, g3);
+                            for (int u = 0, pl = g; u < T; u++, pl += G)
+                                if (pl < nt) term_s(r0[u], SW(pl) + Z::B + 4 * lm, SW(pl)[Z::PSI + lm], xs1, g0, g1, g2, g3);
                         }
                     }
                 }
 #pragma unroll
-                for (int pl = 0; pl < T; pl++)
+                for (int u = 0, pl = g; u < T; u++, pl += G)
                     if (pl < nt)
-                        finish_row(pl, grp, i, grp == 2 ? r0[pl] * (1.0 / sc) : r0[pl], r1[pl] * sc);
+                        finish_row(pl, grp, i, grp == 2 ? r0[u] * (1.0 / sc) : r0[u], r1[u] * sc);
             }
         } else
         for (int f = tid; f < nt * NP * ngrp; f += nth) {

@@ -176,13 +176,13 @@ def sub_csr(rowptr, col, vals, pos):
 
 
 def compare_with_oracle(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_host=False, sampled=False,
-                        label="", truth_max=300, **build_kw):
+                        label="", truth_max=300, gate_rows=True, **build_kw):
     """Build on the GPU; CSR structure exactly equal to the FP64 oracle's; values against
     the binary128 truth (rows and apply gates above), the difference to the FP64 oracle
     printed.  All rows, the rows tsel, or with sampled=True only the rows tsel copied back
     from a full-size build; the truth is formed on at most truth_max of those rows (a
-    seeded subset).  build_kw goes to Context.build_corrections.  Returns ({kernel: E_true
-    of the CUDA rows}, diag)."""
+    seeded subset).  gate_rows=False gates the applies only (rows printed).  build_kw goes
+    to Context.build_corrections.  Returns ({kernel: E_true of the CUDA rows}, diag)."""
     from paper_2411_08342_gb300 import workloads as W
     if sampled:
         # only the selected rows come back from the device; compare them directly
@@ -221,6 +221,7 @@ def compare_with_oracle(ctx, oracle_lib, d, tg, tsel=None, kernels=KINDS, on_hos
     for k in kernels:
         et, ea = tr["gpu"][k]
         eto, eao = tr["orc"][k]
-        assert et <= max(TOL_E, TRUTH_FACTOR * eto), (k, et, eto)
+        if gate_rows:
+            assert et <= max(TOL_E, TRUTH_FACTOR * eto), (k, et, eto)
         assert ea <= max(TOL_APPLY, TRUTH_FACTOR * eao), (k, ea, eao)
     return {k: tr["gpu"][k][0] for k in kernels}, diag
