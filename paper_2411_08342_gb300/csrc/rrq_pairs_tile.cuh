@@ -1167,12 +1167,8 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
         } else
         {
-        // M: rows through the fit matrices (Step 8), jump and smooth subtraction, for the kernel
-        // groups {D, D'} (X_D), {S'} (X_S'), {S} (X_S2, X_S1).  When every pair of the tile is on
-        // one patch (the usual case: the work list is grouped by patch), one thread per
-        // (group, node) reads each fit-matrix entry once and applies it to all the tile's pairs;
-        // otherwise one thread per (group, pair, node).  Both forms take the same operations in
-        // the same order for a pair, so its rows do not depend on the tile it falls in.
+        // M: rows through the fit matrices (Step 8), jump and smooth subtraction, one thread per
+        // (kernel group, pair, node) for the groups {D, D'} (X_D), {S'} (X_S'), {S} (X_S2, X_S1)
         // fit-matrix terms of the lm-th harmonic at one node, FP64 (fused into the sums)
         auto term_d = [&](double &r0, double &r1, const double *B, const double *Bd, double x0, double x1, double x2,
                           double x3) {
@@ -1242,98 +1238,6 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 vS[dst] = r0;
             }
         };
-        const size_t ps0 = (size_t)s_item[0].P;
-        if (s_item[nt - 1].P == s_item[0].P) {
-            const double sc = SW(0)[Z::FR + 12];
-            // G groups of the tile's pairs (pairs g, g + G, ...) so that the items fill the CTA
-            const int nit = NP * ngrp, G = max(1, min(nt, nth / nit));
-            for (int f = tid; f < nit * G; f += nth) {
-                const int g = f / nit, grp = s_grp[(f % nit) / NP], i = f % NP;
-                double r0[T], r1[T];
-                if (MIX) {
-                    dfa a0[T], a1[T];
-#pragma unroll
-                    for (int u = 0, pl = g; u < T; u++, pl += G) a0[u] = a1[u] = dfa{0.f, 0.f};
-                    if (grp == 0) {
-                        const float2 *X = pd.XD2 + ps0 * pd_X(pd.pmax);
-                        for (int lm = 0; lm < NP; lm++) {
-                            const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
-                            const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
-#pragma unroll
-                            for (int u = 0, pl = g; u < T; u++, pl += G)
-                                if (pl < nt)
-                                    mterm_d(a0[u], a1[u], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
-                                            reinterpret_cast<const float2 *>(SW(pl) + Z::BD) + 4 * lm, x0, x1, x2, x3);
-                        }
-                    } else if (grp == 1) {
-                        const float2 *X = pd.XSp2 + ps0 * pd_X(pd.pmax);
-                        for (int lm = 0; lm < NP; lm++) {
-                            const float2 x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
-                            const float2 x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
-#pragma unroll
-                            for (int u = 0, pl = g; u < T; u++, pl += G)
-                                if (pl < nt)
-                                    mterm_sp(a0[u], reinterpret_cast<const float2 *>(SW(pl) + Z::BP) + 4 * lm, x0, x1, x2,
-                                             x3);
-                        }
-                    } else {
-                        const float2 *X = pd.XS22 + ps0 * pd_X(pd.pmax), *X1 = pd.XS12 + ps0 * pd_XS1(pd.pmax);
-                        for (int lm = 0; lm < NP; lm++) {
-                            const float2 xs1 = X1[lm * NP + i];
-                            const float2 g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
-                            const float2 g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
-#pragma unroll
-                            for (int u = 0, pl = g; u < T; u++, pl += G)
-                                if (pl < nt)
-                                    mterm_s(a0[u], reinterpret_cast<const float2 *>(SW(pl) + Z::B) + 4 * lm,
-                                            reinterpret_cast<const float2 *>(SW(pl) + Z::PSI)[lm], xs1, g0, g1, g2, g3);
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0, pl = g; u < T; u++, pl += G) {
-                        r0[u] = dfval(a0[u]);
-                        r1[u] = dfval(a1[u]);
-                    }
-                } else {
-#pragma unroll
-                    for (int u = 0, pl = g; u < T; u++, pl += G) r0[u] = r1[u] = 0.0;
-                    if (grp == 0) {
-                        const double *X = pd.XD + ps0 * pd_X(pd.pmax);
-                        for (int lm = 0; lm < NP; lm++) {
-                            const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
-                            const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
-#pragma unroll
-                            for (int u = 0, pl = g; u < T; u++, pl += G)
-                                if (pl < nt)
-                                    term_d(r0[u], r1[u], SW(pl) + Z::B + 4 * lm, SW(pl) + Z::BD + 4 * lm, x0, x1, x2, x3);
-                        }
-                    } else if (grp == 1) {
-                        const double *X = pd.XSp + ps0 * pd_X(pd.pmax);
-                        for (int lm = 0; lm < NP; lm++) {
-                            const double x0 = X[(0 * NP + lm) * NP + i], x1 = X[(1 * NP + lm) * NP + i];
-                            const double x2 = X[(2 * NP + lm) * NP + i], x3 = X[(3 * NP + lm) * NP + i];
-#pragma unroll
-                            for (int u = 0, pl = g; u < T; u++, pl += G)
-                                if (pl < nt) term_sp(r0[u], SW(pl) + Z::BP + 4 * lm, x0, x1, x2, x3);
-                        }
-                    } else {
-                        const double *X = pd.XS2 + ps0 * pd_X(pd.pmax), *X1 = pd.XS1 + ps0 * pd_XS1(pd.pmax);
-                        for (int lm = 0; lm < NP; lm++) {
-                            const double xs1 = X1[lm * NP + i];
-                            const double g0 = X[(0 * NP + lm) * NP + i], g1 = X[(1 * NP + lm) * NP + i];
-                            const double g2 = X[(2 * NP + lm) * NP + i], g3 = X[(3 * NP + lm) * NP + i];
-#pragma unroll
-                            for (int u = 0, pl = g; u < T; u++, pl += G)
-                                if (pl < nt) term_s(r0[u], SW(pl) + Z::B + 4 * lm, SW(pl)[Z::PSI + lm], xs1, g0, g1, g2, g3);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0, pl = g; u < T; u++, pl += G)
-                    if (pl < nt)
-                        finish_row(pl, grp, i, grp == 2 ? r0[u] * (1.0 / sc) : r0[u], r1[u] * sc);
-            }
-        } else
         for (int f = tid; f < nt * NP * ngrp; f += nth) {
             const int grp = s_grp[f / (nt * NP)], rem = f % (nt * NP), pl = rem / NP, i = rem % NP;
             const double *sw = SW(pl);
