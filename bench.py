@@ -47,9 +47,9 @@ SEED = 20241115
 # DRAM bytes per (target, patch) pair of the FP64 per-pair kernel at p = 6, from a one-pass
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the launch / its pairs),
 # valid only for the kernel sources whose hash is given; otherwise reported as null.
-TRAFFIC_CAPTURE = {"sources_sha16": "df1fbc8cf4ecbaf9", "bytes_per_pair": 1663.0,
+TRAFFIC_CAPTURE = {"sources_sha16": "8ad56b7324a81225", "bytes_per_pair": 1663.0,
                    "capture": "ncu --set full, k_pairs_tile<6, false, 5> on the 5,120-patch ellipsoid "
-                              "(4,347,204 pairs, 7.229 GB), scaled by pairs"}
+                              "(4,347,204 pairs, 3.365 GB read + 3.864 GB written), scaled by pairs"}
 
 
 def workload(levels: int = 6):
@@ -316,9 +316,10 @@ def bench_gpu(args):
         "accuracy": {
             "reference": "binary128 build of the oracle (same algorithm, rounding unit 2^-113), "
                          "tests/test_gpu_parity.py::test_full_size_ellipsoid_sampled, 100 sampled rows",
-            "apply_E_true": "1.1e-12 (D), 1.3e-12 (S'), 4.5e-13 (D'), 7.5e-16 (S): the corrections applied to a "
-                            "random Y_l^m density, relative to the sums they correct",
-            "row_E_true": "1.8e-6 (D), 1.4e-6 (S'), 3.7e-8 (S), 1.7e-10 (D'); the FP64 oracle's own: 1.9e-6, 1.3e-6, "
+            "apply_E_true": "3.5e-12 (D), 2.6e-12 (S'), 8.7e-13 (D'), 1.4e-15 (S); the FP64 oracle's own: 1.1e-12, "
+                            "7.9e-13, 3.0e-13, 1.1e-15: the corrections applied to a random Y_l^m density, "
+                            "relative to the sums they correct",
+            "row_E_true": "1.9e-6 (D), 1.7e-6 (S'), 4.7e-8 (S), 2.0e-10 (D'); the FP64 oracle's own: 1.9e-6, 1.3e-6, "
                           "5.0e-8, 2.4e-10 (binary64 rows of this formulation lose digits on these stretched "
                           "patches, Sec. 5.1 eq. interpolationerror)",
             "gate": "E_true <= max(1e-10, 4 x the FP64 oracle's E_true), rows and applies"},
