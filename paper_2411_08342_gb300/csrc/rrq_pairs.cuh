@@ -31,7 +31,7 @@ constexpr int WARPS = 4;
 // Per-pair shared-memory layout (in doubles).  Regions whose lifetimes do not overlap share
 // space, so that more pairs' CTAs fit on an SM:
 //   header YT, NUT, XT, NT, FR                 whole tile
-//   ST, GST, HST (target harmonic tables)     phases C/D .. L
+//   ST, GST (target harmonics, gradients)     phases C/D .. L
 //   OM (Omega_0, Omega and nu' derivatives)   H .. L
 //   R: WV (premultiplied sample vectors)      H .. K, holding before H the edge
 //      coefficients EA (A .. D) and after K the nu'-derivative table DST and (mixed)
@@ -50,8 +50,7 @@ struct PairSm {
     static constexpr int YT = 0, NUT = 3, XT = 6, NT = 9, FR = 12;   // FR: 16
     static constexpr int ST = 28;                                     // NJK complex
     static constexpr int GST = ST + 2 * NJK;                          // NJK*3 complex
-    static constexpr int HST = GST + 6 * NJK;                         // NJK*6 complex
-    static constexpr int OM = HST + 12 * NJK;                         // 8
+    static constexpr int OM = GST + 6 * NJK;                          // 8
     static constexpr int R = OM + 8;
     static constexpr int WV = R;                                      // NS*12
     static constexpr int EA = R;                                      // 9P

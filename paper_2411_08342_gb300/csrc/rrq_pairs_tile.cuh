@@ -238,14 +238,15 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
             }
         }
         __syncthreads();
-        // D: target gradients / Hessians; monomial edge coefficients
+        // D: target gradients (the Hessians are formed where they are used, phase L); monomial
+        // edge coefficients
         for (int f = tid; f < nt * (NJK + 9 * P); f += nth) {
             const int pl = f / (NJK + 9 * P), it = f % (NJK + 9 * P);
             double *sw = SW(pl);
             if (it < NJK) {
                 const int jk = it;
                 const cd *St = reinterpret_cast<const cd *>(sw + Z::ST);
-                cd *gSt = reinterpret_cast<cd *>(sw + Z::GST), *HSt = reinterpret_cast<cd *>(sw + Z::HST);
+                cd *gSt = reinterpret_cast<cd *>(sw + Z::GST);
                 int j = 0;
                 while (jk_index(j + 1, 0) <= jk) j++;
                 const int k = jk - jk_index(j, 0);
@@ -253,17 +254,6 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 gSt[3 * jk + 0] = tget(St, j - 1, k);
                 gSt[3 * jk + 1] = cscale(csub(a, b), 0.5);
                 gSt[3 * jk + 2] = cmuli(cscale(cadd(a, b), 0.5));
-                if (wantDP) {
-                    const cd r0 = tget(St, j - 2, k), rm1 = tget(St, j - 2, k - 1), rp1 = tget(St, j - 2, k + 1);
-                    const cd rm2 = tget(St, j - 2, k - 2), rp2 = tget(St, j - 2, k + 2);
-                    cd *H = HSt + 6 * jk;
-                    H[0] = r0;
-                    H[1] = cscale(csub(rm1, rp1), 0.5);
-                    H[2] = cmuli(cscale(cadd(rm1, rp1), 0.5));
-                    H[3] = cscale(cadd(csub(rm2, cscale(r0, 2.0)), rp2), 0.25);
-                    H[4] = cmuli(cscale(csub(rm2, rp2), 0.25));
-                    H[5] = cscale(cadd(cadd(rm2, cscale(r0, 2.0)), rp2), -0.25);
-                }
             } else {
                 const int w = it - NJK;
                 const int e = w / (3 * P), rem = w % (3 * P), kk = rem / 3, a = rem % 3;
@@ -768,7 +758,6 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                              double Ip, double dI0, double dI1, double dI2, double dI3) {
             const double *nut = sw + Z::NUT, *Om = sw + Z::OM;
             const cd *St = reinterpret_cast<const cd *>(sw + Z::ST), *gSt = reinterpret_cast<const cd *>(sw + Z::GST);
-            const cd *HSt = reinterpret_cast<const cd *>(sw + Z::HST);
             const cd *g = gSt + 3 * jk_index(l, m);
             const double W0 = Om[0], W1 = Om[1], W2 = Om[2], W3 = Om[3];
             const cd G0 = cscale(cadd(cadd(cscale(g[0], W1), cscale(g[1], W2)), cscale(g[2], W3)), -1.0);
@@ -801,7 +790,19 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 const cd E1 = cadd(cscale(g[0], X0), csub(cscale(g[2], X2), cscale(g[1], X3)));
                 const cd E2 = cadd(cscale(g[1], X0), csub(cscale(g[0], X3), cscale(g[2], X1)));
                 const cd E3 = cadd(cscale(g[2], X0), csub(cscale(g[1], X1), cscale(g[0], X2)));
-                const cd *H = HSt + 6 * jk_index(l, m);
+                // Hessian of S^{(l,m)} at y' by the ladder rules applied twice: the second
+                // derivatives of Rn_l^m are combinations of Rn_{l-2}^{m-2 .. m+2}
+                cd H[6];
+                {
+                    const cd r0 = tget(St, l - 2, m), rm1 = tget(St, l - 2, m - 1), rp1 = tget(St, l - 2, m + 1);
+                    const cd rm2 = tget(St, l - 2, m - 2), rp2 = tget(St, l - 2, m + 2);
+                    H[0] = r0;
+                    H[1] = cscale(csub(rm1, rp1), 0.5);
+                    H[2] = cmuli(cscale(cadd(rm1, rp1), 0.5));
+                    H[3] = cscale(cadd(csub(rm2, cscale(r0, 2.0)), rp2), 0.25);
+                    H[4] = cmuli(cscale(csub(rm2, rp2), 0.25));
+                    H[5] = cscale(cadd(cadd(rm2, cscale(r0, 2.0)), rp2), -0.25);
+                }
                 cd hn[3];
                 hn[0] = cadd(cadd(cscale(H[0], nut[0]), cscale(H[1], nut[1])), cscale(H[2], nut[2]));
                 hn[1] = cadd(cadd(cscale(H[1], nut[0]), cscale(H[3], nut[1])), cscale(H[4], nut[2]));
