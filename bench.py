@@ -47,9 +47,10 @@ SEED = 20241115
 # DRAM bytes per (target, patch) pair of the FP64 per-pair kernel at p = 6, from a one-pass
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the launch / its pairs),
 # valid only for the kernel sources whose hash is given; otherwise reported as null.
-TRAFFIC_CAPTURE = {"sources_sha16": "8ad56b7324a81225", "bytes_per_pair": 1663.0,
-                   "capture": "ncu --set full, k_pairs_tile<6, false, 5> on the 5,120-patch ellipsoid "
-                              "(4,347,204 pairs, 3.365 GB read + 3.864 GB written), scaled by pairs"}
+TRAFFIC_CAPTURE = {"sources_sha16": "450d4754ced8ce17", "bytes_per_pair": 1663.0,
+                   "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, k_pairs_tile<6, false, 5> "
+                              "on the 5,120-patch ellipsoid (4,347,204 pairs, 3.318 GB read + 3.910 GB written), "
+                              "scaled by pairs"}
 
 
 def workload(levels: int = 6):
