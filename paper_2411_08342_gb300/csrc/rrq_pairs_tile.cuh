@@ -423,14 +423,18 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                 for (int i = 0; i < 12; i++) o[i] = vv[i];
             }
         }
-        // (2) Omega_0 on graded panels, one warp per (pair, edge), so that the warps share the
-        // edges evenly whatever the tile size; per-edge partial sums in shared memory
-        for (int pe = warp; pe < nt * 3; pe += nwarp) {
+        // (2) Omega_0 on graded panels, one half-warp per (pair, edge): an edge away from the
+        // target has one panel of RRQ_NOM = 16 points, which fills a half-warp, and the
+        // half-warps share the edges evenly whatever the tile size; per-edge partial sums in
+        // shared memory
+        for (int pe0 = 2 * warp; pe0 < nt * 3; pe0 += 2 * nwarp) {
+            const int pe = pe0 + (lane >> 4), hl = lane & 15;
+            double o0 = 0.0, do0 = 0.0;
+            if (pe < nt * 3) {
             const int pl = pe / 3, e = pe % 3;
             double *sw = SW(pl);
             const double *yt = sw + Z::YT, *nut = sw + Z::NUT, *t0s = sw + Z::T0, *em = sw + Z::EM;
             const double uz = s_uz[pl];
-            double o0 = 0.0, do0 = 0.0;
             const double nxu0 = uz * nut[1], nxu1 = -uz * nut[0], nuu = nut[2] * uz;
             {
                 const double *cm = em + 3 * P * e;
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     const dfa n0 = {nf[0].x, nf[0].y}, n1 = {nf[1].x, nf[1].y}, n2 = {nf[2].x, nf[2].y};
                     const float uzf = (float)uz;
                     dfa a0acc = {0.0f, 0.0f}, a1acc = {0.0f, 0.0f};
-                    for (int idx = lane; idx < npan * RRQ_NOM; idx += 32) {
+                    for (int idx = hl; idx < npan * RRQ_NOM; idx += 16) {
                         const int pan = idx / RRQ_NOM, g = idx % RRQ_NOM;
                         dfa a0, a1;
                         if (pan < nl) {
@@ -513,7 +517,7 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     o0 = dfval(a0acc);
                     do0 = dfval(a1acc);
                 } else
-                for (int idx = lane; idx < npan * RRQ_NOM; idx += 32) {
+                for (int idx = hl; idx < npan * RRQ_NOM; idx += 16) {
                     const int pan = idx / RRQ_NOM, g = idx % RRQ_NOM;
                     // panel k away from the central one spans (2^(k-1) - 1) sig .. (2^k - 1) sig
                     // beyond lo (or hi): widths sig, 2 sig, 4 sig, ...
@@ -552,9 +556,10 @@ __global__ void __launch_bounds__(128) k_pairs_tile(const PairArgs a, unsigned l
                     }
                 }
             }
-            o0 = warp_sum(o0);
-            if (wantDP) do0 = warp_sum(do0);
-            if (lane == 0) {
+            }
+            o0 = half_warp_sum(o0);
+            if (wantDP) do0 = half_warp_sum(do0);
+            if (hl == 0 && pe < nt * 3) {
                 s_h0[pe] = o0;
                 s_h1[pe] = do0;
             }
